@@ -1,0 +1,305 @@
+"""Seeded synthetic inputs for the kernel memory guard.
+
+This module only *places* things: guard-table ranges laid out in a virtual-address
+window, and access streams aimed at chosen places in that layout, each access carrying
+the class it was aimed at (its label). It computes no guard verdict: the classification
+rule of the protected memory model (Sec. IV-E, Sec. V-C) lives in the oracle and in the
+CUDA library, and neither is imported here. Both sides consume these inputs.
+
+Randomness is a counter-based stream: word i of stream (seed, tag) is
+splitmix64(key ^ (i * 0x9E3779B97F4A7C15)) with key = splitmix64(seed ^ tag * C),
+where splitmix64 is the finaliser of Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators" (OOPSLA 2014). Zipf draws use the rejection-inversion
+method of Hoermann and Derflinger, "Rejection-inversion to generate variates from
+monotone discrete distributions" (ACM TOMACS 1996), in float64 on the host.
+
+Kinds: 0 = user allocation, 1 = protected kernel/module memory, 2 = MMIO aperture
+(Table I). Labels use the verdict codes 0 = allow, 1 = protected, 2 = MMIO,
+3 = straddle, 4 = unmapped, 5 = invalid.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+U64 = np.uint64
+GOLDEN = U64(0x9E3779B97F4A7C15)
+
+KIND_USER, KIND_PROTECTED, KIND_MMIO = 0, 1, 2
+LABEL_ALLOW, LABEL_PROTECTED, LABEL_MMIO, LABEL_STRADDLE, LABEL_UNMAPPED, LABEL_INVALID = range(6)
+
+# Table I of the paper: the prototype's fixed virtual-address apertures.
+TABLE1_MMIO = (0xF0000000000, 0xF1000000000)
+TABLE1_PROTECTED = (0xF1000000000, 0xF8000000000)
+TABLE1_USER = (0xF8000000000, 0x108000000000)
+
+SEED_BASE = 0xA61E0500
+WIDTHS = np.array([1, 2, 4, 8, 16], dtype=np.uint8)
+
+KiB = 1 << 10
+MiB = 1 << 20
+GiB = 1 << 30
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser on a uint64 array (wrapping arithmetic)."""
+    z = np.asarray(x, dtype=U64) + GOLDEN
+    z = (z ^ (z >> U64(30))) * U64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> U64(27))) * U64(0x94D049BB133111EB)
+    return z ^ (z >> U64(31))
+
+
+class Stream:
+    """Counter-based random stream; every draw advances the counter by its length."""
+
+    def __init__(self, seed: int, tag: int = 0):
+        mix = np.array([(seed ^ (tag * 0x2545F4914F6CDD1D)) & (2**64 - 1)], dtype=U64)
+        self.key = splitmix64(mix)[0]
+        self.ctr = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        idx = np.arange(self.ctr, self.ctr + n, dtype=U64)
+        self.ctr += n
+        return splitmix64(self.key ^ (idx * GOLDEN))
+
+    def uniform(self, n: int) -> np.ndarray:
+        """float64 in [0, 1) from the top 53 bits."""
+        return (self.u64(n) >> U64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+    def below(self, hi, n: int) -> np.ndarray:
+        """Integers in [0, hi) (hi scalar or array, each < 2**53), as int64."""
+        hi = np.asarray(hi, dtype=np.float64)
+        r = np.floor(self.uniform(n) * hi).astype(np.int64)
+        return np.minimum(r, np.asarray(hi, dtype=np.int64) - 1)
+
+    def log_uniform(self, lo: int, hi: int, n: int) -> np.ndarray:
+        """Integers log-uniform in [lo, hi]."""
+        u = self.uniform(n)
+        v = np.floor(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
+        return np.clip(v, lo, hi)
+
+    def permutation(self, n: int) -> np.ndarray:
+        return np.argsort(self.u64(n), kind="stable")
+
+    def choice(self, options: np.ndarray, n: int) -> np.ndarray:
+        return options[self.below(len(options), n)]
+
+
+def zipf(stream: Stream, s: float, n_max: int, count: int) -> np.ndarray:
+    """Zipf(s) ranks in [1, n_max] by rejection-inversion (Hoermann & Derflinger 1996).
+
+    The hat is the integral of x**-s; a candidate k is accepted when it falls in the
+    region under the step function h(k) = k**-s. Valid for s > 1.
+    """
+    one_m_s = 1.0 - s
+
+    def H(x):
+        return np.power(x, one_m_s) / one_m_s
+
+    def H_inv(y):
+        return np.power(y * one_m_s, 1.0 / one_m_s)
+
+    h_x1 = H(1.5) - 1.0
+    h_n = H(n_max + 0.5)
+    squeeze = 2.0 - H_inv(H(2.5) - 2.0 ** (-s))
+    out = np.empty(count, dtype=np.int64)
+    todo = np.arange(count)
+    while todo.size:
+        u = h_n + stream.uniform(todo.size) * (h_x1 - h_n)
+        x = H_inv(u)
+        k = np.clip(np.floor(x + 0.5), 1, n_max)
+        ok = (k - x <= squeeze) | (u >= H(k + 0.5) - np.power(k, -s))
+        out[todo[ok]] = k[ok].astype(np.int64)
+        todo = todo[~ok]
+    return out
+
+
+@dataclass
+class Ranges:
+    """A guard table as the caller hands it over: parallel arrays, any order."""
+
+    base: np.ndarray  # uint64
+    size: np.ndarray  # uint64
+    kind: np.ndarray  # uint32
+    ident: np.ndarray  # uint32, caller tag reported in violation records
+    meta: dict = field(default_factory=dict)
+
+    def __len__(self):
+        return len(self.base)
+
+    def shifted(self, delta: int) -> "Ranges":
+        return Ranges(self.base + U64(delta), self.size.copy(), self.kind.copy(),
+                      self.ident.copy(), dict(self.meta))
+
+    def concat(self, other: "Ranges") -> "Ranges":
+        return Ranges(np.concatenate([self.base, other.base]),
+                      np.concatenate([self.size, other.size]),
+                      np.concatenate([self.kind, other.kind]),
+                      np.concatenate([self.ident, other.ident]), dict(self.meta))
+
+
+def _ranges(base, size, kind, ident, **meta) -> Ranges:
+    return Ranges(np.asarray(base, dtype=U64), np.asarray(size, dtype=U64),
+                  np.asarray(kind, dtype=np.uint32), np.asarray(ident, dtype=np.uint32), meta)
+
+
+def table1_apertures() -> Ranges:
+    """Table I as a three-range table: MMIO, protected and user apertures."""
+    spans = [TABLE1_MMIO, TABLE1_PROTECTED, TABLE1_USER]
+    return _ranges([s[0] for s in spans], [s[1] - s[0] for s in spans],
+                   [KIND_MMIO, KIND_PROTECTED, KIND_USER], [2, 1, 0])
+
+
+def _round_up(x, m):
+    return (x + m - 1) // m * m
+
+
+def layout(stream: Stream, sizes: np.ndarray, kinds: np.ndarray, span: int, base: int,
+           min_gap: int = 4 * KiB, align: int = 256) -> Ranges:
+    """Place ranges of the given sizes/kinds in shuffled order inside [base, base+span).
+
+    Each range starts on an `align` boundary, its size is kept exact (not rounded), and
+    every range is preceded and followed by a hole of at least `min_gap` bytes; the
+    leftover span is split at random among the holes. Range i of the input gets ident
+    0x1000 + i. The result is returned in an order that differs from address order.
+    """
+    n = len(sizes)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    kinds = np.asarray(kinds)
+    order = stream.permutation(n)          # address order -> input index
+    footprint = int(_round_up(sizes, align).sum())
+    holes = n + 1
+    units = (span - footprint) // align
+    min_units = min_gap // align
+    extra = units - holes * min_units
+    if extra < 0:
+        raise ValueError("span too small for the requested ranges")
+    w = stream.uniform(holes) + 1e-9
+    share = np.floor(w / w.sum() * extra).astype(np.int64)
+    share[-1] += extra - share.sum()
+    gap = (share + min_units) * align
+    starts = np.empty(n, dtype=np.int64)
+    cur = base + int(gap[0])
+    for slot in range(n):
+        i = order[slot]
+        starts[i] = cur
+        cur += int(_round_up(int(sizes[i]), align)) + int(gap[slot + 1])
+    shuffle = stream.permutation(n)        # output position -> input index
+    return _ranges(starts[shuffle], sizes[shuffle], kinds[shuffle], 0x1000 + shuffle,
+                   span_lo=base, span_hi=base + span)
+
+
+def find(r: Ranges, ident: int) -> int:
+    """Base address of the range carrying `ident`."""
+    return int(r.base[np.flatnonzero(r.ident == ident)[0]])
+
+
+def batch_table(seed: int = SEED_BASE + 1, span: int = GiB, base: int = TABLE1_USER[0],
+                n_user: int = 64, n_prot: int = 16, n_mmio: int = 4) -> Ranges:
+    """The batch-check table: 64 user (4 KiB-8 MiB), 16 protected (64 KiB-1 MiB) and
+    4 MMIO (4 KiB-64 KiB) ranges in a 1 GiB window starting at the user aperture."""
+    st = Stream(seed, 1)
+    sizes = np.concatenate([st.log_uniform(4 * KiB, 8 * MiB, n_user),
+                            st.log_uniform(64 * KiB, MiB, n_prot),
+                            st.log_uniform(4 * KiB, 64 * KiB, n_mmio)])
+    kinds = np.array([KIND_USER] * n_user + [KIND_PROTECTED] * n_prot + [KIND_MMIO] * n_mmio)
+    return layout(st, sizes, kinds, span, base)
+
+
+def _sorted(r: Ranges):
+    o = np.argsort(r.base, kind="stable")
+    return r.base[o].astype(np.int64), r.size[o].astype(np.int64), r.kind[o]
+
+
+def batch_accesses(table: Ranges, n: int, seed: int = SEED_BASE + 1,
+                   frac_deny_in=0.04, frac_straddle=0.03, frac_unmapped=0.03):
+    """(address, width, label) triples aimed at the table: inside user allocations,
+    inside protected/MMIO ranges, straddling a user allocation's first or last byte into
+    its neighbouring hole, and inside holes or outside the window. Shuffled.
+
+    Relies on the layout() property that every range is surrounded by holes of at least
+    4 KiB, so a straddle touches exactly one range and a hole access touches none.
+    """
+    st = Stream(seed, 2)
+    base, size, kind = _sorted(table)
+    end = base + size
+    n_in = int(n * frac_deny_in)
+    n_str = int(n * frac_straddle)
+    n_un = int(n * frac_unmapped)
+    n_ok = n - n_in - n_str - n_un
+    addr = np.empty(n, dtype=np.int64)
+    width = np.empty(n, dtype=np.uint8)
+    label = np.empty(n, dtype=np.uint8)
+    users = np.flatnonzero(kind == KIND_USER)
+    denies = np.flatnonzero(kind != KIND_USER)
+    pos = 0
+
+    # inside one user allocation
+    w = st.choice(WIDTHS, n_ok).astype(np.int64)
+    j = users[st.below(len(users), n_ok)]
+    off = st.below(size[j] - w + 1, n_ok)
+    addr[pos:pos + n_ok], width[pos:pos + n_ok], label[pos:pos + n_ok] = base[j] + off, w, LABEL_ALLOW
+    pos += n_ok
+
+    # inside a protected or MMIO range
+    if n_in:
+        w = st.choice(WIDTHS, n_in).astype(np.int64)
+        j = denies[st.below(len(denies), n_in)]
+        off = st.below(size[j] - w + 1, n_in)
+        addr[pos:pos + n_in], width[pos:pos + n_in] = base[j] + off, w
+        label[pos:pos + n_in] = np.where(kind[j] == KIND_MMIO, LABEL_MMIO, LABEL_PROTECTED)
+        pos += n_in
+
+    # straddling the first or last byte of a user allocation
+    if n_str:
+        w = st.choice(WIDTHS[1:], n_str).astype(np.int64)
+        j = users[st.below(len(users), n_str)]
+        k = 1 + st.below(w - 1, n_str)
+        at_end = st.below(2, n_str) == 1
+        addr[pos:pos + n_str] = np.where(at_end, end[j] - k, base[j] - k)
+        width[pos:pos + n_str], label[pos:pos + n_str] = w, LABEL_STRADDLE
+        pos += n_str
+
+    # in a hole between ranges, or outside the window
+    if n_un:
+        w = st.choice(WIDTHS, n_un).astype(np.int64)
+        lo = np.concatenate([[table.meta["span_lo"]], end])
+        hi = np.concatenate([base, [table.meta["span_hi"]]])
+        g = st.below(len(lo), n_un)
+        in_hole = st.below(2, n_un) == 0
+        a_hole = lo[g] + st.below(hi[g] - lo[g] - w + 1, n_un)
+        below = st.below(2, n_un) == 0
+        far = st.below(GiB, n_un)
+        a_out = np.where(below, table.meta["span_lo"] - GiB + far - 16,
+                         table.meta["span_hi"] + far)
+        addr[pos:pos + n_un] = np.where(in_hole, a_hole, a_out)
+        width[pos:pos + n_un], label[pos:pos + n_un] = w, LABEL_UNMAPPED
+        pos += n_un
+
+    p = st.permutation(n)
+    return addr[p].astype(U64), width[p], label[p]
+
+
+def stream_layout(n_elems: int, seed: int = SEED_BASE + 2, n_decoys: int = 1021,
+                  n_prot: int = 64, n_mmio: int = 8, decoy_max: int = 8 * MiB):
+    """Arena layout for the guarded streaming kernels: three fp32 arrays a, b, c of
+    n_elems each plus decoy user allocations, protected and MMIO ranges, all carved
+    from one arena the caller owns. Offsets are relative to the arena start.
+
+    Returns (ranges_relative, arena_bytes, {"a": off, "b": off, "c": off}).
+    """
+    st = Stream(seed, 3)
+    arr = n_elems * 4
+    sizes = np.concatenate([[arr, arr, arr],
+                            st.log_uniform(4 * KiB, decoy_max, n_decoys),
+                            st.log_uniform(64 * KiB, MiB, n_prot),
+                            st.log_uniform(4 * KiB, 64 * KiB, n_mmio)])
+    kinds = np.array([KIND_USER] * (3 + n_decoys) + [KIND_PROTECTED] * n_prot
+                     + [KIND_MMIO] * n_mmio)
+    align = 4 * KiB
+    holes = len(sizes) + 1
+    need = int(_round_up(sizes, align).sum()) + holes * 64 * KiB
+    span = _round_up(need, 2 * MiB)
+    r = layout(st, sizes, kinds, span, 0, min_gap=4 * KiB, align=align)
+    return r, span, {name: find(r, 0x1000 + k) for k, name in enumerate("abc")}

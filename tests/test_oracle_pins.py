@@ -1,0 +1,283 @@
+"""Pins for the oracle: checks against facts fixed outside the oracle itself.
+
+- Table I golden cases derived by hand (tests/golden/table1_apertures.txt).
+- Brute force on tiny tables through a per-byte ownership formulation: every byte of a
+  small window is assigned its owning range, and the verdict is read off the set of
+  owners -- a different computation from the oracle's interval compares.
+- The Table I special case as a closed form of four compares.
+- Generator labels: the batch workload's accesses are placed by construction, so the
+  verdict histogram is known exactly.
+- IEEE arithmetic of the reference kernels: scale is one rounded multiply, triad one
+  correctly rounded fused multiply-add, checked with exact rationals.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import agile_synth as syn
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_apertures.txt")
+V = {name: i for i, name in enumerate(oracle.VERDICT_NAMES)}
+M64 = 2**64 - 1
+
+
+def _golden_rows():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        f = line.split()
+        rows.append((f[0], int(f[1], 16), int(f[2], 0), V[f[3]], int(f[4], 16)))
+    return rows
+
+
+@pytest.mark.parametrize("method", ["linear", "sorted"])
+def test_table1_golden_batch(method):
+    rows = [r for r in _golden_rows() if r[0] == "b"]
+    t = syn.table1_apertures()
+    addr = np.array([r[1] for r in rows], dtype=np.uint64)
+    width = np.array([r[2] for r in rows], dtype=np.uint8)
+    v, rid, log = oracle.check_batch(t, addr, width, method=method)
+    assert v.tolist() == [r[3] for r in rows]
+    assert rid.tolist() == [r[4] for r in rows]
+    first = next(i for i, r in enumerate(rows) if r[3] != 0)
+    assert log.key == first and log.count == sum(r[3] != 0 for r in rows)
+
+
+def test_table1_golden_validate():
+    rows = [r for r in _golden_rows() if r[0] == "v"]
+    t = syn.table1_apertures()
+    v, rid = oracle.validate(t, np.array([r[1] for r in rows], dtype=np.uint64),
+                             np.array([r[2] for r in rows], dtype=np.uint64))
+    assert v.tolist() == [r[3] for r in rows]
+    assert rid.tolist() == [r[4] for r in rows]
+
+
+def test_table1_closed_form():
+    """Table I: three abutting apertures, so the rule is four interval compares."""
+    (m0, m1), (p0, p1), (u0, u1) = syn.TABLE1_MMIO, syn.TABLE1_PROTECTED, syn.TABLE1_USER
+    st = syn.Stream(7, 99)
+    edges = np.array([m0, m1, p1, u1], dtype=np.int64)
+    n = 20000
+    a = edges[st.below(4, n)] + st.below(64, n) - 32
+    w = st.choice(syn.WIDTHS, n).astype(np.int64)
+    exp = np.full(n, V["UNMAPPED"])
+    e = a + w
+    exp[(a < u1) & (e > p1)] = V["STRADDLE"]
+    exp[(a < p1) & (e > m1)] = V["PROTECTED"]
+    exp[(a < m1) & (e > m0)] = V["MMIO"]
+    exp[(a >= p1) & (e <= u1)] = V["ALLOW"]
+    v, _, _ = oracle.check_batch(syn.table1_apertures(), a.astype(np.uint64), w.astype(np.uint8))
+    assert (v == exp).all()
+
+
+# ---------------------------------------------------------------- brute force
+
+
+def _tiny_table(st, window_lo, window=192, max_ranges=6):
+    """Random disjoint ranges in a small window, some abutting, some gapped."""
+    k = int(st.below(max_ranges + 1, 1)[0])
+    cuts = np.sort(st.below(window, 2 * k)) if k else np.array([], dtype=np.int64)
+    base, size, kind = [], [], []
+    for i in range(k):
+        lo, hi = int(cuts[2 * i]), int(cuts[2 * i + 1])
+        if st.below(3, 1)[0] == 0 and base:       # abut the previous range
+            lo = base[-1] + size[-1] - window_lo
+        if hi <= lo:
+            continue
+        base.append(window_lo + lo)
+        size.append(hi - lo)
+        kind.append(int(st.below(3, 1)[0]))
+    ident = list(range(100, 100 + len(base)))
+    return syn._ranges(base, size, kind, ident)
+
+
+def _bytewise(t, window_lo, window, a, w):
+    """Verdict and range from the owners of the bytes [a, a+w)."""
+    if w == 0 or a + w > M64:
+        return V["INVALID"], oracle.NO_RANGE
+    owner = {}
+    for j in range(len(t)):
+        for x in range(int(t.base[j]), int(t.base[j] + t.size[j])):
+            owner[x] = j
+    owners = {owner.get(x, -1) for x in range(a, a + w)}
+    if len(owners) == 1 and -1 not in owners:
+        j = next(iter(owners))
+        if t.kind[j] == 0:
+            return V["ALLOW"], int(t.ident[j])
+    owners.discard(-1)
+    for cls, verdict in ((2, "MMIO"), (1, "PROTECTED"), (0, "STRADDLE")):
+        hit = [j for j in owners if t.kind[j] == cls]
+        if hit:
+            j = min(hit, key=lambda j: int(t.base[j]))
+            return V[verdict], int(t.ident[j])
+    return V["UNMAPPED"], oracle.NO_RANGE
+
+
+@pytest.mark.parametrize("window_lo", [0x1000, 2**64 - 192])
+def test_bruteforce_tiny_tables(window_lo):
+    st = syn.Stream(11, window_lo & 0xFFFF)
+    window = 192
+    for trial in range(40):
+        t = _tiny_table(st, window_lo, window)
+        assert oracle.table_check(t) == 0
+        lo = max(window_lo - 20, 0)
+        hi = min(window_lo + window + 4, M64)
+        addrs, widths = [], []
+        for a in range(lo, hi):
+            for w in (1, 2, 3, 4, 8, 16, 17):
+                addrs.append(a)
+                widths.append(w)
+        addrs = np.array(addrs, dtype=np.uint64)
+        widths = np.array(widths, dtype=np.uint64)
+        exp = [_bytewise(t, window_lo, window, int(a), int(w)) for a, w in zip(addrs, widths)]
+        ev = np.array([e[0] for e in exp])
+        er = np.array([e[1] for e in exp])
+        v, rid = oracle.validate(t, addrs, widths)
+        assert (v == ev).all() and (rid == er).all()
+        # batch form: widths outside {1,2,4,8,16} are invalid
+        bv, brid, log = oracle.check_batch(t, addrs, widths.astype(np.uint8), method="linear")
+        sv, srid, slog = oracle.check_batch(t, addrs, widths.astype(np.uint8), method="sorted")
+        legal = np.isin(widths, [1, 2, 4, 8, 16])
+        assert (bv[legal] == ev[legal]).all() and (bv[~legal] == V["INVALID"]).all()
+        assert (brid[legal] == er[legal]).all()
+        assert (sv == bv).all() and (srid == brid).all() and slog == log
+        viol = np.flatnonzero(bv != 0)
+        assert log.count == len(viol)
+        if len(viol):
+            i = int(viol[0])
+            assert (log.key, log.addr, log.width, log.verdict, log.range_id) == \
+                (i, int(addrs[i]), int(widths[i]), int(bv[i]), int(brid[i]))
+
+
+def test_table_rules():
+    ok = syn._ranges([0, 16, 32], [16, 16, 1], [0, 0, 1], [1, 2, 3])
+    assert oracle.table_check(ok) == 0                       # abutting ranges are legal
+    assert oracle.table_check(syn._ranges([0, 15], [16, 4], [0, 1], [1, 2])) == 3
+    assert oracle.table_check(syn._ranges([0], [0], [0], [1])) == 1
+    assert oracle.table_check(syn._ranges([M64], [1], [0], [1])) == 2
+    assert oracle.table_check(syn._ranges([M64 - 1], [1], [0], [1])) == 0
+    assert oracle.table_check(syn._ranges([0], [1], [3], [1])) == 4
+
+
+def test_abutting_allocations_straddle():
+    """Two user allocations side by side stay two: an access across both is denied."""
+    t = syn._ranges([0x1000, 0x1010], [16, 16], [0, 0], [7, 8])
+    v, rid, _ = oracle.check_batch(t, np.array([0x100C, 0x1008, 0x1010], np.uint64),
+                                   np.array([8, 8, 16], np.uint8))
+    assert v.tolist() == [V["STRADDLE"], V["ALLOW"], V["ALLOW"]]
+    assert rid.tolist() == [7, 7, 8]
+
+
+# ---------------------------------------------------------------- generator labels
+
+
+def test_batch_workload_labels_small():
+    t = syn.batch_table()
+    assert oracle.table_check(t) == 0
+    addr, width, label = syn.batch_accesses(t, 200_000)
+    n = len(addr)
+    counts = np.bincount(label, minlength=6)
+    assert counts[V["STRADDLE"]] == n * 3 // 100 and counts[V["UNMAPPED"]] == n * 3 // 100
+    assert counts[V["PROTECTED"]] + counts[V["MMIO"]] == n * 4 // 100
+    v_lin, rid_lin, log_lin = oracle.check_batch(t, addr, width, method="linear")
+    assert (v_lin == label).all()
+    v_s, rid_s, log_s = oracle.check_batch(t, addr, width, method="sorted")
+    assert (v_s == v_lin).all() and (rid_s == rid_lin).all() and log_s == log_lin
+    assert log_lin.key == int(np.flatnonzero(label != 0)[0])
+    assert log_lin.count == int((label != 0).sum())
+
+
+def test_batch_workload_full_size_sorted():
+    """1M accesses, the sorted oracle; labels hold exactly (90/4/3/3 split)."""
+    t = syn.batch_table()
+    addr, width, label = syn.batch_accesses(t, 1 << 20)
+    v, _, log = oracle.check_batch(t, addr, width, method="sorted")
+    assert (v == label).all()
+    assert log.count == (1 << 20) - int((label == 0).sum())
+
+
+# ---------------------------------------------------------------- reference kernels
+
+
+def _f32_neighbours(r):
+    r = np.float32(r)
+    return np.nextafter(r, np.float32(-np.inf)), np.nextafter(r, np.float32(np.inf))
+
+
+def _is_correct_rounding(exact: Fraction, r: np.float32) -> bool:
+    lo, hi = _f32_neighbours(r)
+    d = abs(exact - Fraction(float(r)))
+    dl = abs(exact - Fraction(float(lo)))
+    dh = abs(exact - Fraction(float(hi)))
+    if d < dl and d < dh:
+        return True
+    if d == dl or d == dh:                 # tie: even significand wins
+        return (np.float32(r).view(np.uint32) & 1) == 0
+    return False
+
+
+def test_reference_kernels_ieee():
+    st = syn.Stream(5, 1)
+    n = 3000
+    b = (st.uniform(n) * 2 - 1).astype(np.float32) * np.float32(2.0) ** st.below(40, n).astype(np.float32)
+    c = (st.uniform(n) * 2 - 1).astype(np.float32)
+    s = 3.0
+    assert (oracle.stream_plain("copy", b, None).view(np.uint32) == b.view(np.uint32)).all()
+    scaled = oracle.stream_plain("scale", b, None, s)
+    assert (scaled == np.float32(s) * b).all()
+    tri = oracle.stream_plain("triad", b, c, s)
+    for i in range(n):
+        exact = Fraction(float(np.float32(s))) * Fraction(float(c[i])) + Fraction(float(b[i]))
+        assert _is_correct_rounding(exact, tri[i]), i
+
+
+def test_stream_guard_no_violation_equals_plain():
+    """Sec. V-E / Fig. 2 caption: accesses to user allocations stay on the normal path,
+    so a guarded kernel with no violation computes what the unguarded one does."""
+    n = 1003
+    r, span, off = syn.stream_layout(n, n_decoys=20, n_prot=4, n_mmio=2, decoy_max=64 * 1024)
+    base = 0x7F0000000000
+    t = r.shifted(base)
+    va = {k: base + v for k, v in off.items()}
+    st = syn.Stream(3, 3)
+    b = st.uniform(n).astype(np.float32)
+    c = st.uniform(n).astype(np.float32)
+    for op in ("copy", "scale", "triad"):
+        for pol in ("poison", "sink", "report"):
+            got, log = oracle.stream(op, t, va, b, c, np.zeros(n, np.float32), 3.0, pol)
+            assert (got == oracle.stream_plain(op, b, c, 3.0)).all()
+            assert log.count == 0
+
+
+def test_stream_guard_poison_protected_window():
+    """A protected range laid over part of b: every 16-byte (or tail 4-byte) unit that
+    touches it reads 0 under poison and is logged; report keeps the data."""
+    n = 4 * 64 + 3
+    base = 0x10000
+    va = {"b": base, "c": base + 0x10000, "a": base + 0x20000}
+    prot_lo, prot_len = base + 100, 300                # bytes [100, 400) of b
+    t = syn._ranges([base, base + 0x10000, base + 0x20000, prot_lo],
+                    [100, 4 * n, 4 * n, prot_len], [0, 0, 0, 1], [1, 2, 3, 9])
+    # b is the user range [base, base+100) plus a tail user range after the protected one
+    t = t.concat(syn._ranges([prot_lo + prot_len], [4 * n - 100 - prot_len], [0], [4]))
+    st = syn.Stream(4, 4)
+    b = st.uniform(n).astype(np.float32) + 1
+    got, log = oracle.stream("copy", t, va, b, None, np.full(n, -1, np.float32), 1.0, "poison")
+    units = n // 4
+    starts = np.concatenate([np.arange(units) * 16, units * 16 + np.arange(n - units * 4) * 4])
+    widths = np.concatenate([np.full(units, 16), np.full(n - units * 4, 4)])
+    hit = (starts < 100 + prot_len) & (starts + widths > 100)
+    cross = hit & ((starts < 100) | (starts + widths > 100 + prot_len))
+    elem_hit = np.concatenate([np.repeat(hit[:units], 4), hit[units:]])
+    assert (got[elem_hit] == 0).all() and (got[~elem_hit] == b[~elem_hit]).all()
+    assert log.count == int(hit.sum())
+    assert log.addr == base + int(starts[hit][0]) and log.site == 0
+    assert log.verdict == V["PROTECTED"] and log.range_id == 9
+    assert cross.sum() == 1          # the unit across byte 100 touches user and protected: PROTECTED
+    got_r, log_r = oracle.stream("copy", t, va, b, None, np.zeros(n, np.float32), 1.0, "report")
+    assert (got_r == b).all() and log_r == log
