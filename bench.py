@@ -1,0 +1,407 @@
+"""Benchmark of the kernel memory guard on B300.
+
+Workload (one step): the guarded streaming kernels -- copy a = b, scale a = s*b and
+triad a = b + s*c -- over three fp32 arrays of 2^28 elements (1 GiB each) that live in
+an arena described by a 1096-range guard table (1024 user allocations, 64 protected
+ranges, 8 MMIO ranges; 2 MiB pages), poison policy, violation log reset each step.
+Metric: guarded HBM GB/s = algorithmic bytes (8 + 8 + 12 bytes per element) / time.
+Beside it: the unguarded twins (guarded/unguarded ratio), the batch check's
+checks/s on the 1M-access table workload and on a 2^28-access stream, the roofline of
+the dominant kernel, an end-to-end figure through host buffers, and the oracle timed on
+the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import agile_synth as syn  # noqa: E402
+
+N_ELEMS = 1 << 28
+BYTES_PER_ELEM = {"copy": 8, "scale": 8, "triad": 12}
+STEP_BYTES = sum(BYTES_PER_ELEM.values()) * N_ELEMS
+METRIC = "guarded HBM GB/s (guarded streaming copy+scale+triad; guarded/unguarded ratio, " \
+         "guard checks/s beside)"
+WORKLOAD = ("guarded streaming copy/scale/triad, 3 fp32 arrays of 2^28 elements (1 GiB each) "
+            "in an arena under a 1096-range guard table (1024 user, 64 protected, 8 MMIO), "
+            "2 MiB pages, poison policy")
+KERNEL_SOURCES = ["paper_2606_06697_b300/csrc/stream.cu",
+                  "paper_2606_06697_b300/csrc/guard_device.cuh"]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_tag):
+    """dram bytes per launch recorded by an ncu capture of the same kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_hash(KERNEL_SOURCES)
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel_tag and f[1] == want:
+            return int(f[2])
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.seek(0)
+        rows = [r.split(", ") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (IndexError, ValueError):
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle timing
+
+
+def oracle_sample(n_sample: int, seed: int = 1):
+    """Oracle guarded copy/scale/triad over the first n_sample elements of the workload's
+    arrays, in the workload's arena layout. Returns (seconds, bytes)."""
+    import oracle
+    r, span, off = syn.stream_layout(N_ELEMS)
+    base = 0x7F0000000000
+    t = r.shifted(base)
+    va = {k: base + v for k, v in off.items()}
+    st = syn.Stream(seed, 8)
+    b = st.uniform(n_sample).astype(np.float32)
+    c = st.uniform(n_sample).astype(np.float32)
+    a0 = np.zeros(n_sample, np.float32)
+    t0 = time.perf_counter()
+    for op in ("copy", "scale", "triad"):
+        oracle.stream(op, t, va, b, c, a0, 3.0, "poison")
+    dt = time.perf_counter() - t0
+    return dt, sum(BYTES_PER_ELEM.values()) * n_sample
+
+
+def run_reference(args, ws, rank):
+    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    dt, _ = oracle_sample(1 << 16)                       # calibrate
+    per_elem = dt / (1 << 16)
+    budget = 90.0 / max(args.steps + args.warmup, 1)     # whole run ~1.5 min
+    n_sample = int(max(1 << 12, min(1 << 24, budget / per_elem)))
+    n_sample -= n_sample % 4
+    for _ in range(args.warmup):
+        oracle_sample(n_sample)
+    tot_t, tot_b = 0.0, 0
+    for _ in range(args.steps):
+        dt, nb = oracle_sample(n_sample)
+        tot_t += dt
+        tot_b += nb
+    value = tot_b / tot_t / 1e9
+    sample = (f"first {n_sample} elements of each array per step (of 2^28), same arena table; "
+              f"single-threaded oracle (sorted-interval search per 16-byte access)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": N_ELEMS, "sample_elements": n_sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2606_06697_b300 as ag
+
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    stream = torch.cuda.Stream(device=dev)
+    hbm_peak, peak_kind = peaks()
+
+    r, span, off = syn.stream_layout(N_ELEMS)
+    arena = torch.empty(span, dtype=torch.uint8, device=dev)
+    base = arena.data_ptr()
+    rt = r.shifted(base)
+    tbl = ag.agile_guard_table_build(rt.base, rt.size, rt.kind, rt.ident, 21)
+    tbuf = torch.empty(tbl.device_bytes(), dtype=torch.uint8, device=dev)
+    dtab = tbl.upload(tbuf, stream)
+    A, B, C = (arena[off[k]:off[k] + 4 * N_ELEMS].view(torch.float32) for k in "abc")
+    g = torch.Generator(device=dev).manual_seed(1234 + rank)
+    B.uniform_(-1, 1, generator=g)
+    C.uniform_(-1, 1, generator=g)
+    log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    ops = ("copy", "scale", "triad")
+
+    def step(guarded, ev=None):
+        if guarded:
+            ag.agile_violation_log_init(log, rank, stream)
+        for op in ops:
+            if ev is not None:
+                ev[op][0].record(stream)
+            ag.agile_stream_launch(op, dtab if guarded else None, A, B, C, N_ELEMS, 3.0,
+                                   "poison", log if guarded else None, stream)
+            if ev is not None:
+                ev[op][1].record(stream)
+
+    def timed(guarded, steps, warmup, per_kernel=False):
+        for _ in range(warmup):
+            step(guarded)
+        evs = []
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            ev = None
+            if per_kernel:
+                ev = {op: (torch.cuda.Event(enable_timing=True),
+                           torch.cuda.Event(enable_timing=True)) for op in ops}
+                evs.append(ev)
+            step(guarded, ev)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = t0.elapsed_time(t1)
+        kern = {op: statistics.mean(e[op][0].elapsed_time(e[op][1]) for e in evs) for op in ops} \
+            if per_kernel else None
+        return ms, kern
+
+    # guarded: the headline, with clocks sampled during it
+    clocks = Clocks(local)
+    timed(True, 3, args.warmup)
+    clocks.start()
+    ms, kern = timed(True, args.steps, 0, per_kernel=True)
+    ck = clocks.stop()
+    ms = max_over_ranks(ws, ms, dev)
+    rc, rec = ag.agile_violation_log_read(log, stream)
+    assert rc == 0 and rec.count == 0, "unexpected violation in the guarded workload"
+    value = ws * STEP_BYTES * args.steps / (ms / 1e3) / 1e9
+
+    # unguarded twins
+    ms_u, kern_u = timed(False, max(args.steps // 2, 10), 3, per_kernel=True)
+    value_u = STEP_BYTES * max(args.steps // 2, 10) / (ms_u / 1e3) / 1e9
+
+    # dominant kernel roofline
+    top = max(kern, key=kern.get)
+    achieved = BYTES_PER_ELEM[top] * N_ELEMS / (kern[top] / 1e3) / 1e9
+    traffic = traffic_from_profile(f"stream_{top}_guarded")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "kernel": f"k_stream<{top}, guarded>",
+                "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)"}
+
+    # batch check throughput: the 1M-access table workload and a 2^28-access stream
+    batch = batch_throughput(ag, torch, dev, stream)
+
+    # end to end through host buffers: H2D of b, c, the three guarded kernels, D2H of a
+    e2e_steps = max(3, min(args.steps // 100, 10))
+    hb = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
+    hc = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
+    ha = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
+    hb.copy_(B.cpu())
+    hc.copy_(C.cpu())
+    with torch.cuda.stream(stream):
+        def e2e_step():
+            B.copy_(hb, non_blocking=True)
+            C.copy_(hc, non_blocking=True)
+            step(True)
+            ha.copy_(A, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1), dev)
+    e2e = {"value": ws * STEP_BYTES * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": 2 * 4 * N_ELEMS, "d2h_bytes_per_step": 4 * N_ELEMS,
+           "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        n_sample = 1 << 27
+        dt, nb = oracle_sample(n_sample)
+        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"guarded copy+scale+triad over the first 2^27 of the 2^28 elements, "
+                         f"same arena table, single-threaded oracle; {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements": N_ELEMS, "table_ranges": len(r),
+                       "page_bytes": 1 << 21, "policy": "poison",
+                       "l2": "each array 1 GiB, larger than the 126 MB L2; no flush needed"},
+            "unguarded_gbs": value_u, "guarded_over_unguarded": value / ws / value_u,
+            "kernel_ms": {f"{op}_guarded": kern[op] for op in ops} |
+                         {f"{op}_unguarded": kern_u[op] for op in ops},
+            "roofline": roofline, "batch_check": batch, "e2e": e2e,
+            "gpu_launches": args.steps * 4, "clocks": ck, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def batch_throughput(ag, torch, dev, stream):
+    t = syn.batch_table()
+    tbl = ag.agile_guard_table_build(t.base, t.size, t.kind, t.ident, 21)
+    buf = torch.empty(tbl.device_bytes(), dtype=torch.uint8, device=dev)
+    dtab = tbl.upload(buf, stream)
+    log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, n in (("1M", 1 << 20), ("2^28", 1 << 28)):
+        addr, width, _ = syn.batch_accesses(t, 1 << 20)
+        da = torch.from_numpy(addr.view(np.int64)).to(dev).repeat(n // (1 << 20))
+        dw = torch.from_numpy(width).to(dev).repeat(n // (1 << 20))
+        dv = torch.empty(n, dtype=torch.uint8, device=dev)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        reps = 20 if n == 1 << 20 else 5
+        tot = 0.0
+        for i in range(reps + 3):
+            flush.fill_(i & 0xFF)                          # evict the inputs from L2
+            ag.agile_violation_log_init(log, 0, stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                ag.agile_guard_check_batch(dtab, da, dw, n, dv, log, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        out[name] = {"checks_per_s": n / (ms / 1e3), "ms": ms,
+                     "gbs": n * 10 / (ms / 1e3) / 1e9, "bytes_per_check": 10}
+        del da, dw, dv, flush
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=800)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":                     # host-only: rank 0 runs, others exit
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")),
+                      int(os.environ.get("RANK", "0")))
+        return
+    ws, rank, local = dist_setup()
+    run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,267 @@
+/*
+ * agile_guard.h -- C ABI of the kernel memory guard (B300 / sm_103a).
+ *
+ * The guard enforces the protected GPU memory model of AgileOS (Sec. IV-E, Table I):
+ * device memory is split into user allocations, protected kernel/module memory and
+ * MMIO mappings, and an access -- by a host API call (Sec. V-C) or by an untrusted
+ * kernel (Sec. V-E) -- passes only when its whole byte range lies inside one live user
+ * allocation. Everything else is denied and, under the poison/sink/report policies of
+ * Sec. V-E, logged.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (AGILE_OK) on success, a negative AGILE_ERR_* on a rejected call, or
+ *    AGILE_VIOLATION (> 0) where a call reports that violations were recorded.
+ *    Nothing throws across this boundary. A rejected call launches nothing.
+ *  - "d_" pointers are device pointers (CUDA device memory the caller owns); "h_"
+ *    pointers are host memory. `stream` is a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream). Device work is asynchronous on that stream unless stated.
+ *  - The library owns only what it returns through agile_guard_table_t and the strings
+ *    it hands out (free them with agile_free). Every buffer passed in stays the
+ *    caller's, is never freed by the library and must outlive the work queued on it.
+ *  - Fail closed (Sec. IV-C: unsupported operations fail closed): unknown kinds,
+ *    widths, policies or PTX constructs are rejected or denied, never let through.
+ */
+#ifndef AGILE_GUARD_H
+#define AGILE_GUARD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AGILE_API __attribute__((visibility("default")))
+#else
+#define AGILE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- constants */
+
+/* Range kinds: Table I's three owners of GPU virtual memory. */
+enum { AGILE_USER = 0, AGILE_PROTECTED = 1, AGILE_MMIO = 2 };
+
+/* Verdicts, one byte each. The order of the deny classes (MMIO before protected before
+ * straddle) is this library's reading; the paper gives none. */
+enum {
+    AGILE_ALLOW = 0,          /* inside one user allocation (Sec. IV-E, V-C)          */
+    AGILE_DENY_PROTECTED = 1, /* touches protected kernel/module memory               */
+    AGILE_DENY_MMIO = 2,      /* touches the protected I/O aperture                   */
+    AGILE_DENY_STRADDLE = 3,  /* touches user memory but not inside one allocation    */
+    AGILE_DENY_UNMAPPED = 4,  /* touches no range: hole, freed or unknown address     */
+    AGILE_DENY_INVALID = 5    /* zero or illegal width, or end beyond 2^64-1          */
+};
+
+/* Violation policies (Sec. V-E). TRAP exists only as instrumented PTX text. */
+enum {
+    AGILE_POLICY_POISON = 0,  /* denied loads read 0, denied stores/atomics dropped; logged   */
+    AGILE_POLICY_SINK = 1,    /* denied loads read a zero page, stores go to a sink; logged   */
+    AGILE_POLICY_REPORT = 2,  /* access proceeds unchanged; logged (audit only, not isolating) */
+    AGILE_POLICY_TRAP = 3     /* emit `trap;` before the access (instrumentation only)        */
+};
+
+/* Return codes. */
+enum {
+    AGILE_OK = 0,
+    AGILE_VIOLATION = 1,            /* log holds at least one violation */
+    AGILE_ERR_INVALID_ARG = -1,
+    AGILE_ERR_OVERLAP = -2,         /* two ranges share a byte */
+    AGILE_ERR_ZERO_SIZE = -3,
+    AGILE_ERR_RANGE_OVERFLOW = -4,  /* base + size beyond 2^64 - 1 */
+    AGILE_ERR_BAD_KIND = -5,
+    AGILE_ERR_NOMEM = -6,
+    AGILE_ERR_CUDA = -7,            /* a CUDA runtime call failed */
+    AGILE_ERR_PTX_PARSE = -8,
+    AGILE_ERR_PTX_UNSUPPORTED = -9, /* construct the guard cannot cover: rejected */
+    AGILE_ERR_TIMEOUT = -10,        /* a bounded device wait gave up */
+    AGILE_ERR_TOO_LARGE = -11,
+    AGILE_ERR_ALIGN = -12,          /* pointer alignment the call requires */
+    AGILE_ERR_NOT_FOUND = -13
+};
+
+#define AGILE_NO_RANGE 0xFFFFFFFFu
+#define AGILE_LOG_BYTES 64          /* device bytes of one violation log, 16-byte aligned */
+#define AGILE_MAX_RANGES 0x3FFFFFFFu
+
+/* One range of the guard table: [base, base + size), owned by `kind`. `id` is the
+ * caller's tag for the range, reported in violation records. Sec. V-C: the worker
+ * records each user allocation's base and requested (not rounded) size. */
+typedef struct {
+    uint64_t base;
+    uint64_t size;
+    uint32_t kind;
+    uint32_t id;
+} agile_range_t;
+
+/* Host-side table object (opaque), built once per table version. */
+typedef struct agile_guard_table agile_guard_table_t;
+
+/* Device view of an uploaded table: plain data, copied by value into launches. It is
+ * also stored at the start of the device buffer, so code that holds only the buffer's
+ * address (instrumented PTX) reads the same fields from there. */
+typedef struct {
+    uint64_t lo;              /* first byte of the paged window (page aligned)          */
+    uint64_t npages;          /* pages in the window; page map has npages + 1 entries  */
+    uint32_t log2_page;       /* page size G = 2^log2_page bytes                         */
+    uint32_t n;               /* ranges                                                  */
+    const uint32_t *page;     /* page map (device)                                       */
+    const uint64_t *base;     /* n bases, ascending (device)                            */
+    const uint64_t *end;      /* n exclusive ends (device)                              */
+    const uint32_t *kind;     /* n kinds (device)                                        */
+    const uint32_t *id;       /* n caller tags (device)                                  */
+    void *zero_page;          /* 64 zero bytes read by denied loads under SINK           */
+    void *sink_page;          /* 64 bytes that take denied stores under SINK             */
+    uint64_t bytes;           /* size of the device buffer in use                       */
+} agile_dev_table_t;
+
+/* Decoded violation log. The first fault is the violating access with the smallest
+ * key, an order that does not depend on scheduling: for agile_guard_check_batch the
+ * key is the access index; for guarded kernels it is (address, site), site being the
+ * access's position in the kernel body. */
+typedef struct {
+    uint64_t key;
+    uint64_t addr;
+    uint32_t width;
+    uint32_t verdict;
+    uint32_t site;
+    uint32_t range_id;        /* id of the range that decided the deny, or AGILE_NO_RANGE */
+    uint32_t client;          /* tag given to agile_violation_log_init                   */
+    uint32_t status;          /* 0, or AGILE_LOG_STATUS_* bits                            */
+    uint64_t count;           /* violating accesses; 0 = no violation, other fields 0    */
+} agile_violation_record_t;
+
+#define AGILE_LOG_STATUS_TIMEOUT 1u /* a kernel's bounded wait gave up; results incomplete */
+
+/* ---------------------------------------------------------------- table */
+
+/* Build a table from n ranges in any order (Sec. V-A: the worker records every user
+ * allocation; Sec. IV-E: protected and MMIO ranges). Ranges must be pairwise disjoint,
+ * non-empty, with base + size <= 2^64 - 1 and a known kind; abutting ranges stay
+ * separate (an access across two allocations is a straddle). Errors: OVERLAP,
+ * ZERO_SIZE, RANGE_OVERFLOW, BAD_KIND, TOO_LARGE (n > AGILE_MAX_RANGES), NOMEM,
+ * INVALID_ARG (NULL with n > 0, or log2_page outside [12, 40]). The page size G is
+ * 2^log2_page; it is raised until the page map has at most 2^26 entries. The caller's
+ * array is copied; *out is freed with agile_guard_table_destroy. */
+AGILE_API int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t log2_page,
+                            agile_guard_table_t **out);
+
+/* Device bytes needed by agile_guard_table_upload for this table. */
+AGILE_API int agile_guard_table_device_bytes(const agile_guard_table_t *t, size_t *bytes);
+
+/* Page size actually used (log2), and the number of pages in the map. */
+AGILE_API int agile_guard_table_geometry(const agile_guard_table_t *t, uint32_t *log2_page,
+                               uint64_t *npages);
+
+/* Copy the table into a caller-owned device buffer of at least device_bytes bytes,
+ * 256-byte aligned (ALIGN otherwise), queued on `stream`; fills *out (host) with the
+ * device view. The buffer is read-only to launches afterwards (only the 64-byte sink
+ * page is written, under SINK); a new table version goes to a new buffer. The host
+ * staging copy is owned by `t`, so `t` must stay alive until the stream has run it. */
+AGILE_API int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, void *stream,
+                             agile_dev_table_t *out);
+
+AGILE_API void agile_guard_table_destroy(agile_guard_table_t *t);
+
+/* ---------------------------------------------------------------- host checks */
+
+/* API-time pointer validation (Sec. IV-E, Sec. V-C): for each (h_ptr[i], h_bytes[i])
+ * write the verdict (and, if h_range_id is not NULL, the deciding range id) -- allowed
+ * only when [ptr, ptr + bytes) lies inside one live user allocation; bytes == 0 is
+ * INVALID. Host only, synchronous. Returns AGILE_VIOLATION if any pair was denied. */
+AGILE_API int agile_validate_args(const agile_guard_table_t *t, const uint64_t *h_ptr,
+                        const uint64_t *h_bytes, size_t n, uint8_t *h_verdict,
+                        uint32_t *h_range_id);
+
+/* ---------------------------------------------------------------- violation log */
+
+/* Set a caller-owned AGILE_LOG_BYTES device buffer (16-byte aligned) to the empty log,
+ * tagged with `client`, on `stream`. */
+AGILE_API int agile_violation_log_init(void *d_log, uint32_t client, void *stream);
+
+/* Wait for `stream`, copy the log to the host and decode it. Returns AGILE_VIOLATION
+ * when count > 0 -- the poison policy's "fail at a later synchronization" (Sec. V-E) --
+ * and AGILE_ERR_TIMEOUT when a kernel's bounded wait gave up. */
+AGILE_API int agile_violation_log_read(const void *d_log, agile_violation_record_t *h_out, void *stream);
+
+/* ---------------------------------------------------------------- device checks */
+
+/* Batched guard check: verdict[i] for the access [d_addr[i], d_addr[i] + d_width[i])
+ * (widths 1, 2, 4, 8, 16; anything else is INVALID), by the rule of Sec. IV-E as the
+ * kernel guard applies it (Sec. V-E). Violations go to d_log (first fault = smallest
+ * index) when d_log is not NULL. Layout: SoA, n entries each; any alignment is
+ * accepted (16-byte aligned d_addr and 8-byte aligned d_width/d_verdict take the
+ * vector path). A violation is not an error: returns 0 once queued. */
+AGILE_API int agile_guard_check_batch(const agile_dev_table_t *tbl, const uint64_t *d_addr,
+                            const uint8_t *d_width, size_t n, uint8_t *d_verdict, void *d_log,
+                            void *stream);
+
+/* ---------------------------------------------------------------- guarded kernels */
+
+enum { AGILE_OP_COPY = 0, AGILE_OP_SCALE = 1, AGILE_OP_TRIAD = 2 };
+
+/* Streaming kernels with the guard fused in by hand (Sec. V-E's check before every
+ * global access): COPY a = b, SCALE a = s*b, TRIAD a = b + s*c as one fused
+ * multiply-add. fp32, n elements; a, b, c 16-byte aligned (ALIGN otherwise), c ignored
+ * unless TRIAD. Access order per 16-byte unit: load b (site 0), load c (site 1, triad),
+ * store a (site 1, or 2 for triad); elements past the last whole unit use 4-byte
+ * accesses. `policy` is POISON, SINK or REPORT. Violations go to d_log when it is not
+ * NULL. tbl == NULL runs the unguarded twin (no checks, same code shape), for
+ * measuring the guard's cost. */
+AGILE_API int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *d_a, const float *d_b,
+                        const float *d_c, size_t n, float s, int policy, void *d_log,
+                        void *stream);
+
+/* ---------------------------------------------------------------- PTX guard pass */
+
+typedef struct {
+    int policy;                    /* AGILE_POLICY_*                                     */
+    const char *const *skip;       /* functions left unguarded (trusted module bodies,   */
+    size_t nskip;                  /*   Sec. V-E); may be NULL                            */
+} agile_instrument_opts_t;
+
+typedef struct {
+    uint32_t functions;            /* .entry/.func bodies seen                           */
+    uint32_t guarded;              /* global accesses given a guard                      */
+    uint32_t generic_guarded;      /* generic-space accesses guarded behind isspacep     */
+    uint32_t skipped;              /* accesses left alone inside skipped functions       */
+} agile_instrument_report_t;
+
+/* Instrument PTX text (Sec. V-E): before every ld/st/atom/red on global memory
+ * (and every generic-space one that resolves to global) insert the guard sequence for
+ * `policy`; functions named in opts->skip stay unguarded. The table address comes from
+ * a module-scope `.global .u64 __agile_guard_table` and the log from
+ * `__agile_guard_log`, so kernel signatures do not change. Bulk/tensor copies and
+ * other forms the guard cannot cover are rejected (PTX_UNSUPPORTED). *out (NUL
+ * terminated, length *out_len) is freed with agile_free. Host only. */
+AGILE_API int agile_guard_instrument_ptx(const char *ptx, size_t len, const agile_instrument_opts_t *opts,
+                               char **out, size_t *out_len, agile_instrument_report_t *report);
+
+/* A loaded instrumented module (opaque). */
+typedef struct agile_module agile_module_t;
+
+/* Load instrumented PTX into the current device's context (JIT for sm_103a). */
+AGILE_API int agile_module_load(const char *ptx, agile_module_t **out);
+
+/* Point the module's guard globals at an uploaded table's device buffer and a log
+ * (synchronous copies). */
+AGILE_API int agile_module_bind(agile_module_t *m, const agile_dev_table_t *tbl, void *d_log, void *stream);
+
+/* Launch kernel `name` of the module: grid and block sizes, `args` = array of
+ * pointers to each kernel parameter (cudaLaunchKernel convention). */
+AGILE_API int agile_module_launch(agile_module_t *m, const char *name, uint32_t grid, uint32_t block,
+                        void **args, void *stream);
+
+AGILE_API void agile_module_unload(agile_module_t *m);
+
+/* ---------------------------------------------------------------- misc */
+
+AGILE_API void agile_free(void *p);
+const char *agile_strerror(int code);
+/* Library version as 0xMMmmpp. */
+AGILE_API uint32_t agile_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGILE_GUARD_H */

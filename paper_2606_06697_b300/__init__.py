@@ -1,0 +1,14 @@
+"""Kernel memory guard for B300 (sm_103a): Python binding of ``libagileguard.so``.
+
+Argument marshalling only. Every step of the guard runs in the C/CUDA library; PyTorch
+supplies device memory and streams. The names match the C entry points declared in
+``include/agile_guard.h``. Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+from .abi import (  # noqa: F401
+    AgileError, DevTable, Module, Table, ViolationRecord, agile_free, agile_guard_check_batch,
+    agile_guard_instrument_ptx, agile_guard_table_build, agile_module_bind, agile_module_launch,
+    agile_module_load, agile_module_unload, agile_stream_launch, agile_strerror,
+    agile_validate_args, agile_version, agile_violation_log_init, agile_violation_log_read, lib,
+    library_path, LOG_BYTES, NO_RANGE, VERDICTS, KINDS, POLICIES, OPS)

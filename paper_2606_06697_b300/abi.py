@@ -1,0 +1,345 @@
+"""ctypes binding of the C ABI in ``include/agile_guard.h`` (same names, same arguments).
+
+Host arrays are numpy; device buffers are anything with ``data_ptr()`` (torch tensors)
+or a raw integer address; streams are ``torch.cuda.Stream`` objects, raw cudaStream_t
+integers, or None for the legacy default stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libagileguard.so")
+
+LOG_BYTES = 64
+NO_RANGE = 0xFFFFFFFF
+VERDICTS = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID"]
+KINDS = {"user": 0, "protected": 1, "mmio": 2}
+POLICIES = {"poison": 0, "sink": 1, "report": 2, "trap": 3}
+OPS = {"copy": 0, "scale": 1, "triad": 2}
+
+
+class AgileError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {agile_strerror(code)} ({code})")
+
+
+class _Range(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_uint64), ("size", ctypes.c_uint64),
+                ("kind", ctypes.c_uint32), ("id", ctypes.c_uint32)]
+
+
+class _DevTable(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("npages", ctypes.c_uint64),
+                ("log2_page", ctypes.c_uint32), ("n", ctypes.c_uint32),
+                ("page", ctypes.c_void_p), ("base", ctypes.c_void_p), ("end", ctypes.c_void_p),
+                ("kind", ctypes.c_void_p), ("id", ctypes.c_void_p),
+                ("zero_page", ctypes.c_void_p), ("sink_page", ctypes.c_void_p),
+                ("bytes", ctypes.c_uint64)]
+
+
+class _Record(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_uint64), ("addr", ctypes.c_uint64), ("width", ctypes.c_uint32),
+                ("verdict", ctypes.c_uint32), ("site", ctypes.c_uint32),
+                ("range_id", ctypes.c_uint32), ("client", ctypes.c_uint32),
+                ("status", ctypes.c_uint32), ("count", ctypes.c_uint64)]
+
+
+class _InstrOpts(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int), ("skip", ctypes.POINTER(ctypes.c_char_p)),
+                ("nskip", ctypes.c_size_t)]
+
+
+class _InstrReport(ctypes.Structure):
+    _fields_ = [("functions", ctypes.c_uint32), ("guarded", ctypes.c_uint32),
+                ("generic_guarded", ctypes.c_uint32), ("skipped", ctypes.c_uint32)]
+
+
+_P = ctypes.c_void_p
+_SIG = {
+    "agile_guard_table_build": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, _P]),
+    "agile_guard_table_device_bytes": (ctypes.c_int, [_P, _P]),
+    "agile_guard_table_geometry": (ctypes.c_int, [_P, _P, _P]),
+    "agile_guard_table_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "agile_guard_table_destroy": (None, [_P]),
+    "agile_validate_args": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P]),
+    "agile_violation_log_init": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
+    "agile_violation_log_read": (ctypes.c_int, [_P, _P, _P]),
+    "agile_guard_check_batch": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+    "agile_stream_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
+                                           ctypes.c_float, ctypes.c_int, _P, _P]),
+    "agile_guard_instrument_ptx": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, _P, _P, _P, _P]),
+    "agile_module_load": (ctypes.c_int, [ctypes.c_char_p, _P]),
+    "agile_module_bind": (ctypes.c_int, [_P, _P, _P, _P]),
+    "agile_module_launch": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32,
+                                           _P, _P]),
+    "agile_module_unload": (None, [_P]),
+    "agile_free": (None, [_P]),
+    "agile_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "agile_version": (ctypes.c_uint32, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library. Raises if it is missing: there is no fallback path."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise ImportError(f"{library_path} is missing: build it with "
+                              "`python -m paper_2606_06697_b300.build`")
+        L = ctypes.CDLL(library_path)
+        for name, (res, args) in _SIG.items():
+            try:
+                f = getattr(L, name)
+            except AttributeError:
+                continue            # calling it raises AttributeError: never a silent path
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str, ok=(0,)) -> int:
+    if rc not in ok:
+        raise AgileError(rc, where)
+    return rc
+
+
+def _dptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def agile_strerror(code: int) -> str:
+    return lib().agile_strerror(code).decode()
+
+
+def agile_version() -> int:
+    return lib().agile_version()
+
+
+def agile_free(p) -> None:
+    lib().agile_free(p)
+
+
+# ---------------------------------------------------------------- table
+
+
+class DevTable:
+    """An uploaded table: the device view plus a reference to its buffer."""
+
+    def __init__(self, view: _DevTable, buf):
+        self.view = view
+        self.buf = buf
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.view)
+
+    @property
+    def address(self) -> int:
+        return _dptr(self.buf)
+
+
+class Table:
+    """Host table object; frees itself."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.agile_guard_table_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def device_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().agile_guard_table_device_bytes(self._h, ctypes.byref(n)),
+               "agile_guard_table_device_bytes")
+        return n.value
+
+    def geometry(self):
+        lg = ctypes.c_uint32()
+        npg = ctypes.c_uint64()
+        _check(lib().agile_guard_table_geometry(self._h, ctypes.byref(lg), ctypes.byref(npg)),
+               "agile_guard_table_geometry")
+        return lg.value, npg.value
+
+    def upload(self, buf, stream=None) -> DevTable:
+        """agile_guard_table_upload into `buf` (a uint8 CUDA tensor of >= device_bytes)."""
+        v = _DevTable()
+        nbytes = buf.numel() * buf.element_size() if hasattr(buf, "numel") else self.device_bytes()
+        _check(lib().agile_guard_table_upload(self._h, _dptr(buf), nbytes, _stream(stream),
+                                              ctypes.byref(v)), "agile_guard_table_upload")
+        return DevTable(v, buf)
+
+
+def agile_guard_table_build(base, size, kind, ident, log2_page: int = 21) -> Table:
+    """Build a table from parallel arrays (any order)."""
+    base = _np(base, np.uint64)
+    n = len(base)
+    arr = (_Range * max(n, 1))()
+    raw = np.frombuffer(arr, dtype=np.dtype([("base", "<u8"), ("size", "<u8"),
+                                             ("kind", "<u4"), ("id", "<u4")]), count=max(n, 1))
+    if n:
+        raw["base"] = base
+        raw["size"] = _np(size, np.uint64)
+        raw["kind"] = _np(kind, np.uint32)
+        raw["id"] = _np(ident, np.uint32)
+    out = ctypes.c_void_p()
+    _check(lib().agile_guard_table_build(arr, n, log2_page, ctypes.byref(out)),
+           "agile_guard_table_build")
+    return Table(out.value)
+
+
+def agile_validate_args(table: Table, ptr, nbytes):
+    """Returns (rc, verdict uint8[n], range_id uint32[n]); rc 0 or AGILE_VIOLATION."""
+    ptr = _np(ptr, np.uint64)
+    nbytes = _np(nbytes, np.uint64)
+    v = np.empty(len(ptr), np.uint8)
+    rid = np.empty(len(ptr), np.uint32)
+    rc = _check(lib().agile_validate_args(table.handle, ptr.ctypes.data, nbytes.ctypes.data,
+                                          len(ptr), v.ctypes.data, rid.ctypes.data),
+                "agile_validate_args", ok=(0, 1))
+    return rc, v, rid
+
+
+# ---------------------------------------------------------------- log
+
+
+@dataclass(frozen=True)
+class ViolationRecord:
+    key: int
+    addr: int
+    width: int
+    verdict: int
+    site: int
+    range_id: int
+    client: int
+    status: int
+    count: int
+
+
+def agile_violation_log_init(d_log, client: int = 0, stream=None) -> None:
+    _check(lib().agile_violation_log_init(_dptr(d_log), client, _stream(stream)),
+           "agile_violation_log_init")
+
+
+def agile_violation_log_read(d_log, stream=None):
+    """Returns (rc, ViolationRecord); rc 0, AGILE_VIOLATION (1) or AGILE_ERR_TIMEOUT."""
+    r = _Record()
+    rc = _check(lib().agile_violation_log_read(_dptr(d_log), ctypes.byref(r), _stream(stream)),
+                "agile_violation_log_read", ok=(0, 1, -10))
+    return rc, ViolationRecord(r.key, r.addr, r.width, r.verdict, r.site, r.range_id, r.client,
+                               r.status, r.count)
+
+
+# ---------------------------------------------------------------- device checks
+
+
+def agile_guard_check_batch(dev: DevTable, d_addr, d_width, n: int, d_verdict, d_log=None,
+                            stream=None) -> None:
+    _check(lib().agile_guard_check_batch(dev.ref, _dptr(d_addr), _dptr(d_width), n,
+                                         _dptr(d_verdict), _dptr(d_log), _stream(stream)),
+           "agile_guard_check_batch")
+
+
+def agile_stream_launch(op: str, dev: DevTable | None, d_a, d_b, d_c, n: int, s: float = 3.0,
+                        policy: str = "poison", d_log=None, stream=None) -> None:
+    _check(lib().agile_stream_launch(OPS[op], dev.ref if dev is not None else None, _dptr(d_a),
+                                     _dptr(d_b), _dptr(d_c), n, s, POLICIES[policy], _dptr(d_log),
+                                     _stream(stream)), "agile_stream_launch")
+
+
+# ---------------------------------------------------------------- PTX guard pass
+
+
+def agile_guard_instrument_ptx(ptx: str, policy: str = "poison", skip=()):
+    """Returns (instrumented PTX text, report dict)."""
+    names = [s.encode() for s in skip]
+    arr = (ctypes.c_char_p * max(len(names), 1))(*names) if names else None
+    opts = _InstrOpts(POLICIES[policy], ctypes.cast(arr, ctypes.POINTER(ctypes.c_char_p))
+                      if arr is not None else None, len(names))
+    out = ctypes.c_void_p()
+    out_len = ctypes.c_size_t()
+    rep = _InstrReport()
+    data = ptx.encode()
+    _check(lib().agile_guard_instrument_ptx(data, len(data), ctypes.byref(opts), ctypes.byref(out),
+                                            ctypes.byref(out_len), ctypes.byref(rep)),
+           "agile_guard_instrument_ptx")
+    try:
+        text = ctypes.string_at(out.value, out_len.value).decode()
+    finally:
+        lib().agile_free(out)
+    return text, {"functions": rep.functions, "guarded": rep.guarded,
+                  "generic_guarded": rep.generic_guarded, "skipped": rep.skipped}
+
+
+class Module:
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def unload(self):
+        if self._h.value:
+            lib().agile_module_unload(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            if _lib is not None:
+                self.unload()
+        except Exception:
+            pass
+
+
+def agile_module_unload(m: Module) -> None:
+    m.unload()
+
+
+def agile_module_load(ptx: str) -> Module:
+    out = ctypes.c_void_p()
+    _check(lib().agile_module_load(ptx.encode(), ctypes.byref(out)), "agile_module_load")
+    return Module(out.value)
+
+
+def agile_module_bind(m: Module, dev: DevTable, d_log=None, stream=None) -> None:
+    _check(lib().agile_module_bind(m.handle, dev.ref, _dptr(d_log), _stream(stream)),
+           "agile_module_bind")
+
+
+def agile_module_launch(m: Module, name: str, grid: int, block: int, args, stream=None) -> None:
+    """args: list of ctypes scalars (c_uint64 for pointers, c_float, ...)."""
+    arr = (ctypes.c_void_p * max(len(args), 1))(*[ctypes.cast(ctypes.pointer(a), ctypes.c_void_p)
+                                                   for a in args])
+    _check(lib().agile_module_launch(m.handle, name.encode(), grid, block, arr, _stream(stream)),
+           "agile_module_launch")

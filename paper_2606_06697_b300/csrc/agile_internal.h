@@ -1,0 +1,42 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "agile_guard.h"
+
+struct agile_guard_table {
+    uint32_t log2_page = 21;
+    uint64_t lo = 0;
+    uint64_t npages = 0;
+    uint32_t n = 0;
+    std::vector<uint64_t> base, end;      // ascending base, exclusive end
+    std::vector<uint32_t> kind, id;
+    std::vector<uint32_t> page;           // npages + 1 entries
+    std::vector<unsigned char> staging;   // host image of the device buffer
+    size_t off_base = 0, off_end = 0, off_kind = 0, off_id = 0, total = 0;
+};
+
+namespace agile {
+
+// Host form of the rule (same two-level lookup as the device), used by
+// agile_validate_args and by the serving loop's admission checks.
+uint32_t classify_host(const agile_guard_table &t, uint64_t a, uint64_t w, uint32_t *rid);
+
+// Remember the last CUDA error text for agile_strerror-style diagnostics.
+void set_cuda_error(int err, const char *where);
+int sm_count();
+}  // namespace agile
+
+// Internal check for CUDA calls in host code: returns AGILE_ERR_CUDA from the caller.
+#define AGILE_CUDA_TRY(call)                                        \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) {                                    \
+            agile::set_cuda_error((int)e_, #call);                  \
+            return AGILE_ERR_CUDA;                                  \
+        }                                                           \
+    } while (0)

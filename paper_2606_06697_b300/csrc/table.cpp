@@ -1,0 +1,202 @@
+// Guard table: build (sort, validate, page map), upload into a caller-owned device buffer,
+// and the host form of the check used for API-time pointer validation (Sec. V-C: the
+// worker records each user allocation's base and requested size and resolves pointers
+// against that table; Sec. IV-E: protected and MMIO ranges are never valid targets).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "agile_internal.h"
+
+namespace {
+
+constexpr uint32_t PG_MIXED = 0, PG_USER = 1, PG_HOLE = 2, PG_DENY = 3;
+constexpr uint32_t kIdxMask = 0x3FFFFFFFu;
+constexpr uint64_t kMaxPages = 1ull << 26;
+constexpr size_t kHeaderBytes = 128, kZeroOff = 128, kSinkOff = 192, kPageOff = 256;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Pages of the window [lo, lo + npages * G) that covers every range.
+void window(const agile_guard_table &t, uint32_t lg, uint64_t *lo, uint64_t *np) {
+    if (t.n == 0) { *lo = 0; *np = 0; return; }
+    uint64_t first = t.base.front() >> lg;
+    uint64_t last = (t.end.back() - 1) >> lg;   // end >= 1 since sizes are >= 1
+    *lo = first << lg;
+    *np = last - first + 1;
+}
+
+void build_pages(agile_guard_table &t) {
+    const uint64_t G = 1ull << t.log2_page;
+    t.page.assign(t.npages + 1, 0);
+    uint32_t j = 0;
+    for (uint64_t p = 0; p < t.npages; ++p) {
+        uint64_t ps = t.lo + p * G, pe = ps + G;   // pe may wrap to 0 at the very top
+        while (j < t.n && t.end[j] <= ps) ++j;
+        uint32_t type;
+        if (j == t.n || (pe != 0 && t.base[j] >= pe)) {
+            type = PG_HOLE;
+        } else if (t.base[j] <= ps && (pe == 0 ? t.end[j] == 0 : t.end[j] >= pe)) {
+            type = t.kind[j] == AGILE_USER ? PG_USER : PG_DENY;
+        } else {
+            type = PG_MIXED;
+        }
+        t.page[p] = (type << 30) | j;
+    }
+    t.page[t.npages] = (PG_HOLE << 30) | t.n;
+}
+
+}  // namespace
+
+namespace agile {
+
+uint32_t classify_host(const agile_guard_table &t, uint64_t a, uint64_t w, uint32_t *rid) {
+    *rid = AGILE_NO_RANGE;
+    if (w == 0 || a > ~0ull - w) return AGILE_DENY_INVALID;
+    // last range starting at or below a
+    size_t b = std::upper_bound(t.base.begin(), t.base.end(), a) - t.base.begin();
+    size_t first = b;
+    if (b > 0 && t.end[b - 1] > a) {
+        if (t.kind[b - 1] == AGILE_USER && a + w <= t.end[b - 1]) {
+            *rid = t.id[b - 1];
+            return AGILE_ALLOW;
+        }
+        first = b - 1;
+    }
+    int best = 3;
+    for (size_t k = first; k < t.n && t.base[k] < a + w; ++k) {
+        int r = t.kind[k] == AGILE_MMIO ? 0 : t.kind[k] == AGILE_PROTECTED ? 1 : 2;
+        if (r < best) { best = r; *rid = t.id[k]; }
+    }
+    static const uint32_t v[3] = {AGILE_DENY_MMIO, AGILE_DENY_PROTECTED, AGILE_DENY_STRADDLE};
+    return best == 3 ? (uint32_t)AGILE_DENY_UNMAPPED : v[best];
+}
+
+}  // namespace agile
+
+extern "C" {
+
+int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t log2_page,
+                            agile_guard_table_t **out) {
+    if (out == nullptr || (n > 0 && h_ranges == nullptr)) return AGILE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (log2_page < 12 || log2_page > 40) return AGILE_ERR_INVALID_ARG;
+    if (n > AGILE_MAX_RANGES) return AGILE_ERR_TOO_LARGE;
+    for (size_t i = 0; i < n; ++i) {
+        if (h_ranges[i].kind > AGILE_MMIO) return AGILE_ERR_BAD_KIND;
+        if (h_ranges[i].size == 0) return AGILE_ERR_ZERO_SIZE;
+        if (h_ranges[i].base > ~0ull - h_ranges[i].size) return AGILE_ERR_RANGE_OVERFLOW;
+    }
+    agile_guard_table *t = new (std::nothrow) agile_guard_table;
+    if (t == nullptr) return AGILE_ERR_NOMEM;
+    try {
+        std::vector<uint32_t> ord(n);
+        std::iota(ord.begin(), ord.end(), 0u);
+        std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
+            return h_ranges[x].base < h_ranges[y].base;
+        });
+        t->n = (uint32_t)n;
+        t->base.resize(n); t->end.resize(n); t->kind.resize(n); t->id.resize(n);
+        for (size_t i = 0; i < n; ++i) {
+            const agile_range_t &r = h_ranges[ord[i]];
+            t->base[i] = r.base;
+            t->end[i] = r.base + r.size;
+            t->kind[i] = r.kind;
+            t->id[i] = r.id;
+            if (i > 0 && t->base[i] < t->end[i - 1]) { delete t; return AGILE_ERR_OVERLAP; }
+        }
+        uint32_t lg = log2_page;
+        window(*t, lg, &t->lo, &t->npages);
+        while (t->npages > kMaxPages) {
+            ++lg;
+            window(*t, lg, &t->lo, &t->npages);
+        }
+        t->log2_page = lg;
+        build_pages(*t);
+        size_t off = kPageOff + align256((t->npages + 1) * 4);
+        t->off_base = off; off += align256(n * 8);
+        t->off_end = off;  off += align256(n * 8);
+        t->off_kind = off; off += align256(n * 4);
+        t->off_id = off;   off += align256(n * 4);
+        t->total = off;
+        t->staging.assign(t->total, 0);
+        std::memcpy(t->staging.data() + kPageOff, t->page.data(), t->page.size() * 4);
+        if (n) {
+            std::memcpy(t->staging.data() + t->off_base, t->base.data(), n * 8);
+            std::memcpy(t->staging.data() + t->off_end, t->end.data(), n * 8);
+            std::memcpy(t->staging.data() + t->off_kind, t->kind.data(), n * 4);
+            std::memcpy(t->staging.data() + t->off_id, t->id.data(), n * 4);
+        }
+    } catch (const std::bad_alloc &) {
+        delete t;
+        return AGILE_ERR_NOMEM;
+    }
+    *out = t;
+    return AGILE_OK;
+}
+
+int agile_guard_table_device_bytes(const agile_guard_table_t *t, size_t *bytes) {
+    if (t == nullptr || bytes == nullptr) return AGILE_ERR_INVALID_ARG;
+    *bytes = t->total;
+    return AGILE_OK;
+}
+
+int agile_guard_table_geometry(const agile_guard_table_t *t, uint32_t *log2_page,
+                               uint64_t *npages) {
+    if (t == nullptr) return AGILE_ERR_INVALID_ARG;
+    if (log2_page) *log2_page = t->log2_page;
+    if (npages) *npages = t->npages;
+    return AGILE_OK;
+}
+
+int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, void *stream,
+                             agile_dev_table_t *out) {
+    if (t == nullptr || d_buf == nullptr || out == nullptr) return AGILE_ERR_INVALID_ARG;
+    if (bytes < t->total) return AGILE_ERR_TOO_LARGE;
+    if (((uintptr_t)d_buf & 255) != 0) return AGILE_ERR_ALIGN;
+    unsigned char *d = (unsigned char *)d_buf;
+    agile_dev_table_t h;
+    std::memset(&h, 0, sizeof h);
+    h.lo = t->lo;
+    h.npages = t->npages;
+    h.log2_page = t->log2_page;
+    h.n = t->n;
+    h.page = (const uint32_t *)(d + kPageOff);
+    h.base = (const uint64_t *)(d + t->off_base);
+    h.end = (const uint64_t *)(d + t->off_end);
+    h.kind = (const uint32_t *)(d + t->off_kind);
+    h.id = (const uint32_t *)(d + t->off_id);
+    h.zero_page = d + kZeroOff;
+    h.sink_page = d + kSinkOff;
+    h.bytes = t->total;
+    static_assert(sizeof(agile_dev_table_t) <= kHeaderBytes, "header fits");
+    std::memcpy(t->staging.data(), &h, sizeof h);
+    std::memset(t->staging.data() + kZeroOff, 0, 128);
+    AGILE_CUDA_TRY(cudaMemcpyAsync(d_buf, t->staging.data(), t->total, cudaMemcpyHostToDevice,
+                                   (cudaStream_t)stream));
+    *out = h;
+    return AGILE_OK;
+}
+
+void agile_guard_table_destroy(agile_guard_table_t *t) { delete t; }
+
+int agile_validate_args(const agile_guard_table_t *t, const uint64_t *h_ptr,
+                        const uint64_t *h_bytes, size_t n, uint8_t *h_verdict,
+                        uint32_t *h_range_id) {
+    if (t == nullptr || (n > 0 && (h_ptr == nullptr || h_bytes == nullptr || h_verdict == nullptr)))
+        return AGILE_ERR_INVALID_ARG;
+    int any = 0;
+    for (size_t i = 0; i < n; ++i) {
+        uint32_t rid;
+        uint32_t v = agile::classify_host(*t, h_ptr[i], h_bytes[i], &rid);
+        h_verdict[i] = (uint8_t)v;
+        if (h_range_id) h_range_id[i] = rid;
+        any |= v != AGILE_ALLOW;
+    }
+    return any ? AGILE_VIOLATION : AGILE_OK;
+}
+
+}  // extern "C"
