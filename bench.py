@@ -34,6 +34,7 @@ import agile_synth as syn  # noqa: E402
 N_ELEMS = 1 << 28
 BYTES_PER_ELEM = {"copy": 8, "scale": 8, "triad": 12}
 STEP_BYTES = sum(BYTES_PER_ELEM.values()) * N_ELEMS
+PTX_STREAM = os.path.join(ROOT, "paper_2606_06697_b300", "ptx", "stream.ptx")
 METRIC = "guarded HBM GB/s (guarded streaming copy+scale+triad; guarded/unguarded ratio, " \
          "guard checks/s beside)"
 WORKLOAD = ("guarded streaming copy/scale/triad, 3 fp32 arrays of 2^28 elements (1 GiB each) "
@@ -279,10 +280,20 @@ def run_ours(args, ws, rank, local):
     rc, rec = ag.agile_violation_log_read(log, stream)
     assert rc == 0 and rec.count == 0, "unexpected violation in the guarded workload"
     value = ws * STEP_BYTES * args.steps / (ms / 1e3) / 1e9
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "GB/s", "quick": True,
+                              "elements": N_ELEMS, "steps": args.steps, "kernel_ms": kern,
+                              "clocks": ck}), flush=True)
+        return
 
     # unguarded twins
     ms_u, kern_u = timed(False, max(args.steps // 2, 10), 3, per_kernel=True)
     value_u = STEP_BYTES * max(args.steps // 2, 10) / (ms_u / 1e3) / 1e9
+
+    # the same kernels from hand-written PTX through the guard pass (poison)
+    ptx_kern = ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C)
+    ptx_gbs = STEP_BYTES / (sum(ptx_kern.values()) / 1e3) / 1e9
 
     # dominant kernel roofline
     top = max(kern, key=kern.get)
@@ -342,12 +353,43 @@ def run_ours(args, ws, rank, local):
                        "page_bytes": 1 << 21, "policy": "poison",
                        "l2": "each array 1 GiB, larger than the 126 MB L2; no flush needed"},
             "unguarded_gbs": value_u, "guarded_over_unguarded": value / ws / value_u,
+            "ptx_injected_gbs": ptx_gbs, "ptx_injected_kernel_ms": ptx_kern,
             "kernel_ms": {f"{op}_guarded": kern[op] for op in ops} |
                          {f"{op}_unguarded": kern_u[op] for op in ops},
             "roofline": roofline, "batch_check": batch, "e2e": e2e,
             "gpu_launches": args.steps * 4, "clocks": ck, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
+
+
+def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):
+    """Mean kernel time of the PTX-instrumented copy/scale/triad (poison), CUDA events."""
+    import ctypes
+    text, _ = ag.agile_guard_instrument_ptx(open(PTX_STREAM).read(), "poison")
+    mod = ag.agile_module_load(text)
+    ag.agile_violation_log_init(log, 0, stream)
+    ag.agile_module_bind(mod, dtab, log, stream)
+    grid = torch.cuda.get_device_properties(dev).multi_processor_count * 4
+    args = [ctypes.c_uint64(A.data_ptr()), ctypes.c_uint64(B.data_ptr()),
+            ctypes.c_uint64(C.data_ptr()), ctypes.c_uint64(N_ELEMS), ctypes.c_float(3.0)]
+    out = {}
+    for op in ("copy", "scale", "triad"):
+        for _ in range(3):
+            ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, 512, args, stream)
+        evs = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, 512, args, stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        out[op] = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    rc, rec = ag.agile_violation_log_read(log, stream)
+    assert rc == 0 and rec.count == 0, "violation in the PTX-injected run"
+    mod.unload()
+    return out
 
 
 def batch_throughput(ag, torch, dev, stream):
@@ -390,7 +432,14 @@ def main():
     ap.add_argument("--steps", type=int, default=800)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--elements", type=int, default=1 << 28,
+                    help="elements per array (the workload is 2^28; smaller only for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="guarded steps only: no unguarded, PTX, batch, e2e or CPU legs")
     args = ap.parse_args()
+    global N_ELEMS, STEP_BYTES
+    N_ELEMS = args.elements - args.elements % 4
+    STEP_BYTES = sum(BYTES_PER_ELEM.values()) * N_ELEMS
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":                     # host-only: rank 0 runs, others exit
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")),

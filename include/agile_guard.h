@@ -244,11 +244,14 @@ typedef struct agile_module agile_module_t;
 AGILE_API int agile_module_load(const char *ptx, agile_module_t **out);
 
 /* Point the module's guard globals at an uploaded table's device buffer and a log
- * (synchronous copies). */
+ * (d_log may be NULL: violations then go unrecorded). Synchronous. INVALID_ARG for a
+ * module that was not instrumented. */
 AGILE_API int agile_module_bind(agile_module_t *m, const agile_dev_table_t *tbl, void *d_log, void *stream);
 
 /* Launch kernel `name` of the module: grid and block sizes, `args` = array of
- * pointers to each kernel parameter (cudaLaunchKernel convention). */
+ * pointers to each kernel parameter (cudaLaunchKernel convention). An instrumented
+ * module is refused (INVALID_ARG) until agile_module_bind has run; NOT_FOUND for an
+ * unknown kernel name. */
 AGILE_API int agile_module_launch(agile_module_t *m, const char *name, uint32_t grid, uint32_t block,
                         void **args, void *stream);
 
@@ -257,7 +260,7 @@ AGILE_API void agile_module_unload(agile_module_t *m);
 /* ---------------------------------------------------------------- misc */
 
 AGILE_API void agile_free(void *p);
-const char *agile_strerror(int code);
+AGILE_API const char *agile_strerror(int code);
 /* Library version as 0xMMmmpp. */
 AGILE_API uint32_t agile_version(void);
 

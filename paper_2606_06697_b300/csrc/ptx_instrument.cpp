@@ -1,0 +1,518 @@
+// PTX guard pass (Sec. V-E): parse application PTX, insert the kernel memory guard
+// before every global-memory access, and serialize the result for loading.
+//
+// What is guarded: ld, ldu, st, atom and red on the .global state space, and on the
+// generic space when the address resolves to global memory (isspacep.global). Shared,
+// local, const and param accesses are left alone. Functions named in the skip list
+// (trusted module bodies, Sec. V-E) are left untouched. Forms the guard cannot cover --
+// bulk and tensor copies (cp.*), asynchronous stores/reductions, multimem, surfaces,
+// tensormap and discard -- are rejected (fail closed, Sec. IV-C).
+//
+// The inserted sequence, per access of W bytes at effective address a:
+//   fast path (inline): page p = (a - lo) >> log2 G; allowed at once when p is in the
+//   window, the page map entry says all-user, and (a - lo) mod G + W <= G;
+//   slow path: call __agile_guard_check(a, W, site) -- full classification, log on deny;
+//   then the policy: POISON/SINK send a denied load to the zero page; POISON predicates
+//   a denied store/atom/red off (a denied atom's result reads 0), SINK sends it to the
+//   sink page; REPORT changes nothing; TRAP emits `@!ok trap;`.
+// The table's device address is read once per function from the module global
+// __agile_guard_table; site = the access's position in its function.
+#include <cstdlib>
+#include <cstring>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "agile_internal.h"
+#include "ptx_guard_check.inc"
+
+namespace {
+
+struct Fail {
+    int code;
+};
+
+bool is_ident_start(char c) { return std::isalpha((unsigned char)c) || c == '_' || c == '$' || c == '%'; }
+bool is_ident(char c) { return std::isalnum((unsigned char)c) || c == '_' || c == '$'; }
+
+std::string trim(const std::string &s) {
+    size_t a = 0, b = s.size();
+    while (a < b && std::isspace((unsigned char)s[a])) ++a;
+    while (b > a && std::isspace((unsigned char)s[b - 1])) --b;
+    return s.substr(a, b - a);
+}
+
+// Copy of `s` with comments and string literals blanked to spaces (same length), so
+// that positions found in the clean text index the raw text.
+std::string blank_comments(const std::string &s) {
+    std::string c = s;
+    size_t i = 0, n = s.size();
+    while (i < n) {
+        if (s[i] == '/' && i + 1 < n && s[i + 1] == '/') {
+            while (i < n && s[i] != '\n') c[i++] = ' ';
+        } else if (s[i] == '/' && i + 1 < n && s[i + 1] == '*') {
+            size_t e = s.find("*/", i + 2);
+            if (e == std::string::npos) throw Fail{AGILE_ERR_PTX_PARSE};
+            for (; i < e + 2; ++i) if (c[i] != '\n') c[i] = ' ';
+        } else if (s[i] == '"') {
+            size_t e = s.find('"', i + 1);
+            if (e == std::string::npos) throw Fail{AGILE_ERR_PTX_PARSE};
+            for (++i; i < e; ++i) c[i] = ' ';
+            ++i;
+        } else {
+            ++i;
+        }
+    }
+    return c;
+}
+
+int type_bytes(const std::string &t) {
+    static const char *b1[] = {"b8", "u8", "s8"};
+    static const char *b2[] = {"b16", "u16", "s16", "f16", "bf16"};
+    static const char *b4[] = {"b32", "u32", "s32", "f32", "f16x2", "bf16x2"};
+    static const char *b8[] = {"b64", "u64", "s64", "f64"};
+    for (auto x : b1) if (t == x) return 1;
+    for (auto x : b2) if (t == x) return 2;
+    for (auto x : b4) if (t == x) return 4;
+    for (auto x : b8) if (t == x) return 8;
+    if (t == "b128") return 16;
+    return 0;
+}
+
+std::vector<std::string> split_dots(const std::string &op) {
+    std::vector<std::string> out;
+    size_t i = 0;
+    while (i <= op.size()) {
+        size_t j = op.find('.', i);
+        // "::" qualifiers stay attached to their modifier
+        if (j == std::string::npos) j = op.size();
+        out.push_back(op.substr(i, j - i));
+        i = j + 1;
+    }
+    return out;
+}
+
+struct Access {
+    enum Kind { LOAD, STORE, ATOM, RED } kind;
+    bool generic = false;
+    int width = 0;
+    int dest_bits = 0;          // atom: scalar result size, 0 if not zeroable
+    std::string dest;
+};
+
+class Rewriter {
+  public:
+    Rewriter(int policy, const std::set<std::string> &skip) : policy_(policy), skip_(skip) {}
+
+    std::string run(const std::string &ptx) {
+        if (ptx.find("__ag") != std::string::npos) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
+        const std::string clean = blank_comments(ptx);
+        size_t as = clean.find(".address_size");
+        if (as == std::string::npos) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
+        {
+            size_t k = as + 13;
+            while (k < clean.size() && std::isspace((unsigned char)clean[k])) ++k;
+            if (clean.compare(k, 2, "64") != 0) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
+        }
+        size_t inject_at = clean.find('\n', as);
+        if (inject_at == std::string::npos) inject_at = clean.size();
+
+        std::string out;
+        out.reserve(ptx.size() * 3);
+        size_t i = 0, n = clean.size(), stmt_start = 0;
+        bool injected = false;
+        while (i < n) {
+            if (!injected && i >= inject_at) {
+                out.append(ptx, stmt_start, i - stmt_start);
+                out += "\n";
+                out += kGuardCheckPtx;
+                stmt_start = i;
+                injected = true;
+            }
+            char ch = clean[i];
+            if (ch == ';') {
+                ++i;
+                out.append(ptx, stmt_start, i - stmt_start);
+                stmt_start = i;
+            } else if (ch == '{') {
+                size_t close = match_brace(clean, i);
+                std::string header = clean.substr(stmt_start, i - stmt_start);
+                out.append(ptx, stmt_start, i - stmt_start);
+                if (is_function_header(header)) {
+                    std::string body = ptx.substr(i + 1, close - i - 1);
+                    std::string name = function_name(header);
+                    ++rep_.functions;
+                    out += "{";
+                    out += rewrite_body(body, skip_.count(name) != 0);
+                    out += "}";
+                } else {
+                    out.append(ptx, i, close - i + 1);
+                }
+                i = close + 1;
+                stmt_start = i;
+            } else if (ch == '}') {
+                throw Fail{AGILE_ERR_PTX_PARSE};
+            } else {
+                ++i;
+            }
+        }
+        out.append(ptx, stmt_start, n - stmt_start);
+        if (!injected) out += kGuardCheckPtx;
+        // Fail closed: every memory-access opcode word of the input must have been seen
+        // by the statement parser (guarded, skipped, or on a non-global space).
+        if (count_access_words(clean) != rep_.guarded + rep_.skipped + other_space_)
+            throw Fail{AGILE_ERR_PTX_PARSE};
+        return out;
+    }
+
+    agile_instrument_report_t rep_{};
+
+  private:
+    uint32_t other_space_ = 0;
+
+    // Independent count of ld/ldu/st/atom/red opcode words, by a plain word scan.
+    static uint32_t count_access_words(const std::string &clean) {
+        uint32_t c = 0;
+        size_t i = 0, n = clean.size();
+        while (i < n) {
+            if (std::isalpha((unsigned char)clean[i]) &&
+                (i == 0 || !(is_ident(clean[i - 1]) || clean[i - 1] == '.' || clean[i - 1] == '%'))) {
+                size_t e = i;
+                while (e < n && is_ident(clean[e])) ++e;
+                std::string w = clean.substr(i, e - i);
+                if (e < n && clean[e] == '.' &&
+                    (w == "ld" || w == "ldu" || w == "st" || w == "atom" || w == "red"))
+                    ++c;
+                i = e;
+            } else {
+                ++i;
+            }
+        }
+        return c;
+    }
+
+    int policy_;
+    const std::set<std::string> &skip_;
+    int label_ = 0;
+
+    static size_t match_brace(const std::string &clean, size_t open) {
+        int depth = 0;
+        for (size_t k = open; k < clean.size(); ++k) {
+            if (clean[k] == '{') ++depth;
+            else if (clean[k] == '}' && --depth == 0) return k;
+        }
+        throw Fail{AGILE_ERR_PTX_PARSE};
+    }
+
+    static bool has_token(const std::string &h, const char *tok) {
+        size_t p = 0, L = std::strlen(tok);
+        while ((p = h.find(tok, p)) != std::string::npos) {
+            bool left = p == 0 || std::isspace((unsigned char)h[p - 1]);
+            bool right = p + L >= h.size() || !is_ident(h[p + L]);
+            if (left && right) return true;
+            p += L;
+        }
+        return false;
+    }
+
+    static bool is_function_header(const std::string &h) {
+        return has_token(h, ".entry") || has_token(h, ".func");
+    }
+
+    static std::string function_name(const std::string &h) {
+        std::string flat;
+        int depth = 0;
+        for (char c : h) {
+            if (c == '(') ++depth;
+            else if (c == ')') { --depth; flat += ' '; }
+            else if (depth == 0) flat += c;
+        }
+        size_t k = 0;
+        bool after_kw = false;
+        while (k < flat.size()) {
+            while (k < flat.size() && std::isspace((unsigned char)flat[k])) ++k;
+            size_t e = k;
+            while (e < flat.size() && !std::isspace((unsigned char)flat[e])) ++e;
+            std::string tok = flat.substr(k, e - k);
+            if (tok == ".entry" || tok == ".func") after_kw = true;
+            else if (after_kw && !tok.empty() && tok[0] != '.') return tok;
+            k = e;
+        }
+        return "";
+    }
+
+    std::string prologue() const {
+        return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<6>;\n"
+               "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
+               "\tld.global.u64 %__agT7, [__agile_guard_table];\n"
+               "\tld.global.u64 %__agT0, [%__agT7];\n"
+               "\tld.global.u64 %__agT1, [%__agT7+8];\n"
+               "\tld.global.u32 %__agTlg, [%__agT7+16];\n"
+               "\tld.global.u64 %__agT2, [%__agT7+24];\n"
+               "\tld.global.u64 %__agT3, [%__agT7+64];\n"
+               "\tld.global.u64 %__agT4, [%__agT7+72];\n"
+               "\tmov.b64 %__agT5, 1;\n"
+               "\tshl.b64 %__agT5, %__agT5, %__agTlg;\n"
+               "\tsub.s64 %__agT6, %__agT5, 1;\n";
+    }
+
+    std::string rewrite_body(const std::string &body, bool skipped) {
+        const std::string clean = blank_comments(body);
+        std::string out;
+        size_t i = 0, n = clean.size(), stmt = 0;
+        int site = 0;
+        bool any = false;
+        int operand_braces = 0;             // inside a {..} vector operand
+        while (i < n) {
+            char ch = clean[i];
+            if (ch == '{' && (operand_braces > 0 || !only_labels(clean.substr(stmt, i - stmt)))) {
+                ++operand_braces;           // a vector operand, part of the statement
+                ++i;
+            } else if (ch == '}' && operand_braces > 0) {
+                --operand_braces;
+                ++i;
+            } else if (ch == '{' || ch == '}') {
+                out.append(body, stmt, i + 1 - stmt);
+                stmt = ++i;
+            } else if (ch == ';') {
+                if (operand_braces != 0) throw Fail{AGILE_ERR_PTX_PARSE};
+                std::string raw = body.substr(stmt, i + 1 - stmt);
+                std::string cl = clean.substr(stmt, i + 1 - stmt);
+                out += statement(raw, cl, skipped, site, any);
+                stmt = ++i;
+            } else {
+                ++i;
+            }
+        }
+        if (!trim(clean.substr(stmt)).empty()) throw Fail{AGILE_ERR_PTX_PARSE};
+        out.append(body, stmt, n - stmt);
+        return any ? prologue() + out : out;
+    }
+
+    // True when `t` holds nothing but whitespace and labels: a '{' after it opens a scope.
+    static bool only_labels(const std::string &t) {
+        size_t k = 0, n = t.size();
+        for (;;) {
+            while (k < n && std::isspace((unsigned char)t[k])) ++k;
+            if (k == n) return true;
+            size_t e = k;
+            while (e < n && (is_ident(t[e]) || t[e] == '%')) ++e;
+            if (e > k && e < n && t[e] == ':' && (e + 1 >= n || t[e + 1] != ':')) { k = e + 1; continue; }
+            return false;
+        }
+    }
+
+    // One statement (raw text up to and including ';').
+    std::string statement(const std::string &raw, const std::string &cl, bool skipped, int &site,
+                          bool &any) {
+        size_t k = 0, n = cl.size();
+        for (;;) {                          // leading whitespace and labels
+            while (k < n && std::isspace((unsigned char)cl[k])) ++k;
+            size_t e = k;
+            while (e < n && (is_ident(cl[e]) || cl[e] == '%')) ++e;
+            if (e > k && e < n && cl[e] == ':' && (e + 1 >= n || cl[e + 1] != ':')) { k = e + 1; continue; }
+            break;
+        }
+        const size_t start = k;
+        std::string pred;
+        bool neg = false;
+        if (k < n && cl[k] == '@') {
+            ++k;
+            if (k < n && cl[k] == '!') { neg = true; ++k; }
+            size_t e = k;
+            while (e < n && (is_ident(cl[e]) || cl[e] == '%')) ++e;
+            pred = cl.substr(k, e - k);
+            k = e;
+            while (k < n && std::isspace((unsigned char)cl[k])) ++k;
+        }
+        const size_t op_start = k;
+        while (k < n && !std::isspace((unsigned char)cl[k]) && cl[k] != ';') ++k;
+        const std::string opcode = cl.substr(op_start, k - op_start);
+        if (opcode.empty() || opcode[0] == '.') return raw;   // directive
+        std::vector<std::string> mods = split_dots(opcode);
+        const std::string &base = mods[0];
+
+        static const char *rejected[] = {"cp", "multimem", "tensormap", "discard", "sust", "suld",
+                                         "sured", "cp.async"};
+        for (auto r : rejected) if (base == r) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
+        if (base != "ld" && base != "ldu" && base != "st" && base != "atom" && base != "red")
+            return raw;
+
+        bool global = false, other_space = false;
+        int vec = 1, tbytes = 0;
+        for (size_t m = 1; m < mods.size(); ++m) {
+            const std::string &x = mods[m];
+            if (x == "global") global = true;
+            else if (x.rfind("shared", 0) == 0 || x == "local" || x == "const" ||
+                     x.rfind("param", 0) == 0 || x == "tex")
+                other_space = true;
+            else if (x == "async" || x == "bulk" || x == "mmio") throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
+            else if (x == "v2") vec = 2;
+            else if (x == "v4") vec = 4;
+            else if (x == "v8") vec = 8;
+            else if (type_bytes(x)) tbytes = type_bytes(x);
+        }
+        if (other_space) { ++other_space_; return raw; }
+        if (tbytes == 0) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
+
+        size_t lb = cl.find('[', k), rb = lb == std::string::npos ? lb : cl.find(']', lb);
+        if (lb == std::string::npos || rb == std::string::npos) throw Fail{AGILE_ERR_PTX_PARSE};
+
+        Access acc;
+        acc.kind = base == "st" ? Access::STORE : base == "atom" ? Access::ATOM
+                 : base == "red" ? Access::RED : Access::LOAD;
+        acc.generic = !global;
+        acc.width = vec * tbytes;
+        if (acc.kind == Access::ATOM) {
+            std::string d = trim(cl.substr(k, lb - k));
+            if (!d.empty() && d.back() == ',') d.pop_back();
+            d = trim(d);
+            if (vec == 1 && (tbytes == 4 || tbytes == 8) && !d.empty() && d[0] == '%') {
+                acc.dest = d;
+                acc.dest_bits = tbytes * 8;
+            }
+        }
+        if (skipped) {
+            ++rep_.skipped;
+            return raw;
+        }
+        any = true;
+        ++rep_.guarded;
+        if (acc.generic) ++rep_.generic_guarded;
+
+        std::string g;
+        g += raw.substr(0, start);          // leading whitespace, comments, labels
+        g += "\n\t// agile guard: site " + std::to_string(site) + ", " + opcode + ", " +
+             std::to_string(acc.width) + " bytes\n";
+        g += address(trim(cl.substr(lb + 1, rb - lb - 1)));
+        emit_check(g, acc, pred, neg, site);
+        ++site;
+
+        // the access itself, address (and for POISON stores the predicate) rewritten
+        std::string instr = raw.substr(start);
+        const size_t ilb = lb - start, irb = rb - start;
+        std::string addr_reg = "%__agd0";
+        bool new_pred = false;
+        const bool writes = acc.kind != Access::LOAD;
+        if (policy_ == AGILE_POLICY_POISON || policy_ == AGILE_POLICY_SINK) {
+            if (!writes) {
+                g += "\tselp.b64 %__agd5, %__agd0, %__agT3, %__agp3;\n";
+                addr_reg = "%__agd5";
+            } else if (policy_ == AGILE_POLICY_SINK) {
+                g += "\tselp.b64 %__agd5, %__agd0, %__agT4, %__agp3;\n";
+                addr_reg = "%__agd5";
+            } else {
+                if (pred.empty()) g += "\tmov.pred %__agp4, %__agp3;\n";
+                else if (!neg) g += "\tand.pred %__agp4, %__agp3, " + pred + ";\n";
+                else g += "\tnot.pred %__agp4, " + pred + ";\n\tand.pred %__agp4, %__agp4, %__agp3;\n";
+                new_pred = true;
+                if (acc.dest_bits)
+                    g += "\t@!%__agp3 mov.b" + std::to_string(acc.dest_bits) + " " + acc.dest + ", 0;\n";
+            }
+            instr = instr.substr(0, ilb) + "[" + addr_reg + "]" + instr.substr(irb + 1);
+            if (new_pred) {
+                const size_t ops = op_start - start;  // strip the old predicate
+                instr = "@%__agp4 " + instr.substr(ops);
+            }
+        } else if (policy_ == AGILE_POLICY_TRAP) {
+            g += "\t@!%__agp3 trap;\n";
+        }
+        g += "\t" + instr;
+        return g;
+    }
+
+    std::string address(const std::string &inner) {
+        std::string basepart = inner, off;
+        size_t plus = inner.find('+');
+        if (plus != std::string::npos) {
+            basepart = trim(inner.substr(0, plus));
+            off = trim(inner.substr(plus + 1));
+            if (off.empty()) throw Fail{AGILE_ERR_PTX_PARSE};
+        }
+        if (basepart.empty()) throw Fail{AGILE_ERR_PTX_PARSE};
+        std::string s;
+        if (basepart[0] == '%') {
+            s = off.empty() ? "\tmov.b64 %__agd0, " + basepart + ";\n"
+                            : "\tadd.s64 %__agd0, " + basepart + ", " + off + ";\n";
+        } else if (std::isdigit((unsigned char)basepart[0]) || basepart[0] == '-') {
+            s = "\tmov.u64 %__agd0, " + basepart + ";\n";
+            if (!off.empty()) s += "\tadd.s64 %__agd0, %__agd0, " + off + ";\n";
+        } else if (is_ident_start(basepart[0])) {
+            s = "\tmov.u64 %__agd0, " + basepart + ";\n";
+            if (!off.empty()) s += "\tadd.s64 %__agd0, %__agd0, " + off + ";\n";
+        } else {
+            throw Fail{AGILE_ERR_PTX_PARSE};
+        }
+        return s;
+    }
+
+    void emit_check(std::string &g, const Access &acc, const std::string &pred, bool neg, int site) {
+        const std::string W = std::to_string(acc.width);
+        const std::string L = "$__AG_OK_" + std::to_string(label_++);
+        g += "\tsub.s64 %__agd1, %__agd0, %__agT0;\n"
+             "\tshr.u64 %__agd2, %__agd1, %__agTlg;\n"
+             "\tsetp.lt.u64 %__agp0, %__agd2, %__agT1;\n"
+             "\tmov.b32 %__agr0, 0;\n"
+             "\t@%__agp0 shl.b64 %__agd3, %__agd2, 2;\n"
+             "\t@%__agp0 add.s64 %__agd3, %__agd3, %__agT2;\n"
+             "\t@%__agp0 ld.global.nc.u32 %__agr0, [%__agd3];\n"
+             "\tand.b64 %__agd4, %__agd1, %__agT6;\n"
+             "\tadd.s64 %__agd4, %__agd4, " + W + ";\n"
+             "\tsetp.le.u64 %__agp1, %__agd4, %__agT5;\n"
+             "\tshr.u32 %__agr1, %__agr0, 30;\n"
+             "\tsetp.eq.and.u32 %__agp1, %__agr1, 1, %__agp1;\n";
+        if (acc.generic)
+            g += "\tisspacep.global %__agp2, %__agd0;\n"
+                 "\tnot.pred %__agp2, %__agp2;\n"
+                 "\tor.pred %__agp1, %__agp1, %__agp2;\n";
+        if (!pred.empty()) {
+            if (!neg) g += "\tnot.pred %__agp2, " + pred + ";\n\tor.pred %__agp1, %__agp1, %__agp2;\n";
+            else g += "\tor.pred %__agp1, %__agp1, " + pred + ";\n";
+        }
+        g += "\tmov.u32 %__agr2, 1;\n"
+             "\t@%__agp1 bra " + L + ";\n"
+             "\t{\n"
+             "\t.param .b64 __aga;\n\t.param .b32 __agw;\n\t.param .b32 __ags;\n\t.param .b32 __agret;\n"
+             "\tst.param.b64 [__aga], %__agd0;\n"
+             "\tst.param.b32 [__agw], " + W + ";\n"
+             "\tst.param.b32 [__ags], " + std::to_string(site) + ";\n"
+             "\tcall (__agret), __agile_guard_check, (__aga, __agw, __ags);\n"
+             "\tld.param.b32 %__agr2, [__agret];\n"
+             "\t}\n" + L + ":\n"
+             "\tsetp.ne.u32 %__agp3, %__agr2, 0;\n";
+    }
+};
+
+}  // namespace
+
+extern "C" int agile_guard_instrument_ptx(const char *ptx, size_t len,
+                                          const agile_instrument_opts_t *opts, char **out,
+                                          size_t *out_len, agile_instrument_report_t *report) {
+    if (ptx == nullptr || out == nullptr || out_len == nullptr) return AGILE_ERR_INVALID_ARG;
+    *out = nullptr;
+    *out_len = 0;
+    int policy = opts ? opts->policy : AGILE_POLICY_POISON;
+    if (policy < AGILE_POLICY_POISON || policy > AGILE_POLICY_TRAP) return AGILE_ERR_INVALID_ARG;
+    std::set<std::string> skip;
+    if (opts && opts->nskip) {
+        if (opts->skip == nullptr) return AGILE_ERR_INVALID_ARG;
+        for (size_t i = 0; i < opts->nskip; ++i)
+            if (opts->skip[i]) skip.insert(opts->skip[i]);
+    }
+    try {
+        Rewriter rw(policy, skip);
+        std::string text = rw.run(std::string(ptx, len));
+        char *buf = (char *)std::malloc(text.size() + 1);
+        if (buf == nullptr) return AGILE_ERR_NOMEM;
+        std::memcpy(buf, text.data(), text.size());
+        buf[text.size()] = '\0';
+        *out = buf;
+        *out_len = text.size();
+        if (report) *report = rw.rep_;
+        return AGILE_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (const std::bad_alloc &) {
+        return AGILE_ERR_NOMEM;
+    }
+}

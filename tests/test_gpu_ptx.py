@@ -1,0 +1,95 @@
+"""PTX-injected guard on the GPU: hand-written PTX, instrumented by the guard pass,
+JIT-loaded and run against the oracle (outputs and logs, bit for bit)."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import agile_synth as syn
+import oracle
+import paper_2606_06697_b300 as ag
+from gpu_util import DEV, device_table, new_log
+from test_gpu_stream import _fill, _hostile_layout
+
+pytestmark = pytest.mark.gpu
+STREAM = open(os.path.join(os.path.dirname(ag.library_path), "ptx", "stream.ptx")).read()
+# site numbering of the hand-written kernels -> the oracle's (vector and tail share sites)
+SITE_MAP = {"copy": [0, 1, 0, 1], "scale": [0, 1, 0, 1], "triad": [0, 1, 2, 0, 1, 2]}
+
+
+def launch(mod, op, A, B, C, n, s=3.0, grid=148 * 4, block=256):
+    args = [ctypes.c_uint64(A.data_ptr()), ctypes.c_uint64(B.data_ptr()),
+            ctypes.c_uint64(C.data_ptr()), ctypes.c_uint64(n), ctypes.c_float(s)]
+    ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, block, args)
+
+
+@pytest.fixture(scope="module")
+def modules():
+    mods = {p: ag.agile_module_load(ag.agile_guard_instrument_ptx(STREAM, p)[0])
+            for p in ("poison", "sink", "report")}
+    mods["plain"] = ag.agile_module_load(STREAM)
+    yield mods
+    for m in mods.values():
+        m.unload()
+
+
+@pytest.mark.parametrize("n", [5, 1 << 20])
+def test_ptx_no_violation(modules, n):
+    r, span, off = syn.stream_layout(n, n_decoys=40, n_prot=8, n_mmio=2, decoy_max=256 * 1024)
+    arena = torch.empty(span, dtype=torch.uint8, device=DEV)
+    _, dev = device_table(r.shifted(arena.data_ptr()), 21)
+    A, B, C = (arena[off[k]:off[k] + 4 * n].view(torch.float32) for k in "abc")
+    b, c = _fill(n, 3)
+    B.copy_(torch.from_numpy(b))
+    C.copy_(torch.from_numpy(c))
+    for op in ("copy", "scale", "triad"):
+        expect = oracle.stream_plain(op, b, c, 3.0)
+        for p in ("poison", "sink", "report", "plain"):
+            A.fill_(-1.0)
+            log = new_log()
+            if p != "plain":
+                ag.agile_module_bind(modules[p], dev, log)
+            launch(modules[p], op, A, B, C, n)
+            rc, rec = ag.agile_violation_log_read(log)
+            assert rc == 0 and rec.count == 0, (op, p)
+            assert (A.cpu().numpy().view(np.uint32) == expect.view(np.uint32)).all(), (op, p)
+
+
+@pytest.mark.parametrize("n", [4099, (1 << 18) + 1])
+@pytest.mark.parametrize("policy", ["poison", "sink", "report"])
+def test_ptx_violations(modules, policy, n):
+    _, _, nbytes = _hostile_layout(n, 0)
+    arena = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+    base = arena.data_ptr()
+    r, va, _ = _hostile_layout(n, base)
+    _, dev = device_table(r, 12)
+    b, c = _fill(n, 77)
+    A, B, C = (arena[va[k] - base:va[k] - base + 4 * n].view(torch.float32) for k in "abc")
+    B.copy_(torch.from_numpy(b))
+    C.copy_(torch.from_numpy(c))
+    for op in ("copy", "scale", "triad"):
+        a0 = np.full(n, -5.0, np.float32)
+        A.copy_(torch.from_numpy(a0))
+        log = new_log(client=9)
+        ag.agile_module_bind(modules[policy], dev, log)
+        launch(modules[policy], op, A, B, C, n)
+        rc, rec = ag.agile_violation_log_read(log)
+        exp, olog = oracle.stream(op, r, va, b, c if op == "triad" else None, a0, 3.0, policy)
+        assert (A.cpu().numpy().view(np.uint32) == exp.view(np.uint32)).all(), op
+        assert rc == 1 and rec.count == olog.count and rec.client == 9
+        assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
+            (olog.key, olog.addr, olog.width, olog.verdict, olog.range_id), (op, rec, olog)
+        assert SITE_MAP[op][rec.site] == olog.site
+
+
+def test_ptx_launch_refused_until_bound():
+    m = ag.agile_module_load(ag.agile_guard_instrument_ptx(STREAM, "poison")[0])
+    x = torch.zeros(64, dtype=torch.float32, device=DEV)
+    with pytest.raises(ag.AgileError) as e:
+        launch(m, "copy", x, x, x, 64, grid=1, block=32)
+    assert e.value.code == -1
+    with pytest.raises(ag.AgileError):
+        ag.agile_module_launch(m, "no_such_kernel", 1, 32, [])
+    m.unload()

@@ -1,0 +1,125 @@
+"""Host-side checks that need no GPU: the library loads and exports every entry point
+the header declares; table rules and API-time validation match the oracle."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import agile_synth as syn
+import oracle
+import paper_2606_06697_b300 as ag
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+def declared():
+    names = []
+    for h in HEADERS:
+        names += re.findall(r"^AGILE_API\s+[\w\s\*]+?\b(agile_\w+)\s*\(", open(h).read(), re.M)
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared()
+    assert len(names) >= 18
+    L = ag.lib()
+    for name in names:
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", ag.library_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (agile_\w+)", out))
+    assert set(names) == exported
+
+
+def test_strerror_and_version():
+    assert ag.agile_version() == 0x000100
+    assert "overlap" in ag.agile_strerror(-2)
+    assert ag.agile_strerror(12345) == "unknown error"
+
+
+ERR = {1: -3, 2: -4, 3: -2, 4: -5}
+
+
+@pytest.mark.parametrize("case", [
+    ([0, 16, 32], [16, 16, 1], [0, 0, 1]),
+    ([0, 15], [16, 4], [0, 1]),
+    ([0], [0], [0]),
+    ([2**64 - 1], [1], [0]),
+    ([2**64 - 2], [1], [0]),
+    ([0], [1], [3]),
+    ([100, 0, 50], [10, 50, 50], [2, 1, 0]),
+    ([100, 0, 50], [10, 51, 50], [2, 1, 0]),
+])
+def test_table_rules_match_oracle(case):
+    base, size, kind = case
+    r = syn._ranges(base, size, kind, list(range(len(base))))
+    want = oracle.table_check(r)
+    if want == 0:
+        ag.agile_guard_table_build(r.base, r.size, r.kind, r.ident)
+    else:
+        with pytest.raises(ag.AgileError) as e:
+            ag.agile_guard_table_build(r.base, r.size, r.kind, r.ident)
+        assert e.value.code == ERR[want]
+
+
+def test_table_page_geometry():
+    r = syn.batch_table()
+    t = ag.agile_guard_table_build(r.base, r.size, r.kind, r.ident, 21)
+    lg, npages = t.geometry()
+    first, last = int(r.base.min()) >> 21, (int((r.base + r.size).max()) - 1) >> 21
+    assert lg == 21 and npages == last - first + 1 <= 512   # pages from first to last range
+    t1 = syn.table1_apertures()
+    big = ag.agile_guard_table_build(t1.base, t1.size, t1.kind, t1.ident, 12)
+    lg, npages = big.geometry()
+    assert npages <= 1 << 26 and lg > 12       # page size raised to bound the map
+    with pytest.raises(ag.AgileError):
+        ag.agile_guard_table_build(t1.base, t1.size, t1.kind, t1.ident, 11)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_validate_args_matches_oracle(seed):
+    """API-time validation (arbitrary byte counts) against the oracle's linear scan."""
+    t = syn.batch_table(seed=syn.SEED_BASE + 40 + seed)
+    st = syn.Stream(seed, 40)
+    base, size = t.base.astype(np.int64), t.size.astype(np.int64)
+    n = 20000
+    j = st.below(len(t), n)
+    off = st.below(size[j] + 64, n) - 32
+    ptr = (base[j] + off).astype(np.uint64)
+    nbytes = np.where(st.below(4, n) == 0, 0, st.log_uniform(1, 1 << 24, n)).astype(np.uint64)
+    tbl = ag.agile_guard_table_build(t.base, t.size, t.kind, t.ident, 21)
+    rc, v, rid = ag.agile_validate_args(tbl, ptr, nbytes)
+    ov, orid = oracle.validate(t, ptr, nbytes)
+    assert (v == ov).all() and (rid == orid).all()
+    assert rc == (1 if (ov != 0).any() else 0)
+    # the exact whole allocation passes
+    rc, v, _ = ag.agile_validate_args(tbl, t.base, t.size)
+    assert ((v == 0) == (t.kind == 0)).all()
+
+
+def test_validate_args_table1_golden():
+    rows = []
+    for line in open(os.path.join(ROOT, "tests", "golden", "table1_apertures.txt")):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            if f[0] == "v":
+                rows.append((int(f[1], 16), int(f[2], 0), oracle.VERDICT_NAMES.index(f[3])))
+    t = syn.table1_apertures()
+    tbl = ag.agile_guard_table_build(t.base, t.size, t.kind, t.ident)
+    _, v, _ = ag.agile_validate_args(tbl, [r[0] for r in rows], [r[1] for r in rows])
+    assert v.tolist() == [r[2] for r in rows]
+
+
+def test_upload_without_gpu_reports_cuda_error():
+    """Host-only machine: the library loads; a device call fails with AGILE_ERR_CUDA, not a crash."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    t = ag.agile_guard_table_build([0], [16], [0], [1])
+    with pytest.raises(ag.AgileError) as e:
+        t.upload(0x100000)
+    assert e.value.code in (-7,)

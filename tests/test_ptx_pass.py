@@ -1,0 +1,166 @@
+"""The PTX guard pass on hand-written PTX, checked as text (no GPU): every global
+access gets a guard, the policies emit what they should, skipped functions and other
+state spaces stay untouched, uncoverable forms are rejected, and the output assembles
+for sm_103a (ptxas)."""
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import paper_2606_06697_b300 as ag
+
+PTX_DIR = os.path.join(os.path.dirname(ag.library_path), "ptx")
+STREAM = open(os.path.join(PTX_DIR, "stream.ptx")).read()
+HDR = ".version 9.0\n.target sm_103a\n.address_size 64\n"
+
+
+def kernel(body, regs=".reg .b64 %rd<8>;\n.reg .f32 %f<8>;\n.reg .b32 %r<8>;\n.reg .pred %p<4>;",
+           name="k"):
+    return HDR + f".visible .entry {name}(.param .u64 p0)\n{{\n{regs}\nld.param.u64 %rd1, [p0];\n{body}\nret;\n}}\n"
+
+
+def assemble(ptx):
+    if shutil.which("ptxas") is None:
+        pytest.skip("ptxas not found")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "m.ptx")
+        open(src, "w").write(ptx)
+        r = subprocess.run(["ptxas", "-arch=sm_103a", src, "-o", os.path.join(d, "m.cubin")],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
+def sites(text):
+    return re.findall(r"// agile guard: site (\d+), (\S+), (\d+) bytes", text)
+
+
+@pytest.mark.parametrize("policy", ["poison", "sink", "report", "trap"])
+def test_stream_kernels_every_access_guarded(policy):
+    out, rep = ag.agile_guard_instrument_ptx(STREAM, policy)
+    assert rep == {"functions": 3, "guarded": 14, "generic_guarded": 0, "skipped": 0}
+    s = sites(out)
+    assert len(s) == 14
+    assert [x[1] for x in s[:4]] == ["ld.global.v4.f32", "st.global.v4.f32", "ld.global.f32",
+                                     "st.global.f32"]
+    assert [int(x[2]) for x in s[:4]] == [16, 16, 4, 4]
+    assert out.count("call (__agret), __agile_guard_check") == 14
+    # every original global access now follows a guard: none keeps its own address form
+    assert not re.search(r"(ld|st)\.global\.(v4\.)?f32[^;]*\[%rd1[0-9]\]", out) or policy in ("report", "trap")
+    if policy == "trap":
+        assert out.count("@!%__agp3 trap;") == 14
+    else:
+        assert "trap;" not in out
+    if policy == "poison":
+        assert out.count("selp.b64 %__agd5, %__agd0, %__agT3, %__agp3") == 8   # loads -> zero page
+        assert out.count("@%__agp4 st.global") == 6                             # stores predicated
+    if policy == "sink":
+        assert out.count("selp.b64 %__agd5, %__agd0, %__agT4, %__agp3") == 6   # stores -> sink
+    assemble(out)
+
+
+def test_skip_list_leaves_trusted_functions_alone():
+    out, rep = ag.agile_guard_instrument_ptx(STREAM, "poison", skip=["agile_ptx_copy"])
+    assert rep["guarded"] == 10 and rep["skipped"] == 4 and rep["functions"] == 3
+    body = out[out.index(".entry agile_ptx_copy"):out.index(".entry agile_ptx_scale")]
+    assert "agile guard" not in body and "__agT" not in body
+    assemble(out)
+
+
+def test_generic_and_other_spaces():
+    body = """
+    ld.f32 %f1, [%rd1];
+    st.f32 [%rd1+8], %f1;
+    ld.shared.f32 %f2, [%rd1];
+    ld.local.f32 %f3, [%rd1];
+    ld.const.f32 %f4, [%rd1];
+    atom.add.u32 %r1, [%rd1+-4], 1;
+    """
+    regs = ".reg .b64 %rd<8>;\n.reg .f32 %f<8>;\n.reg .b32 %r<8>;"
+    out, rep = ag.agile_guard_instrument_ptx(kernel(body, regs), "poison")
+    assert rep["guarded"] == 3 and rep["generic_guarded"] == 3
+    assert out.count("isspacep.global %__agp2, %__agd0") == 3
+    assert "add.s64 %__agd0, %rd1, 8;" in out and "add.s64 %__agd0, %rd1, -4;" in out
+    assert "ld.shared.f32 %f2, [%rd1];" in out and "ld.local.f32 %f3, [%rd1];" in out
+    assert "@!%__agp3 mov.b32 %r1, 0;" in out                 # denied atom reads 0
+    assemble(out)
+
+
+def test_predicated_accesses_combine_predicates():
+    body = """
+    setp.ne.u64 %p1, %rd1, 0;
+    @%p1 st.global.f32 [%rd1], %f1;
+    @!%p1 ld.global.f32 %f2, [%rd1+4];
+    @%p1 red.global.add.u32 [%rd1], %r1;
+    """
+    out, rep = ag.agile_guard_instrument_ptx(kernel(body), "poison")
+    assert rep["guarded"] == 3
+    assert "and.pred %__agp4, %__agp3, %p1;" in out
+    assert "@%__agp4 st.global.f32 [%__agd0], %f1;" in out
+    assert "@!%p1 ld.global.f32 %f2, [%__agd5];" in out
+    assert "or.pred %__agp1, %__agp1, %p1;" in out            # @!%p1: slow path only if p1 false
+    assemble(out)
+
+
+def test_vector_symbol_and_wide_accesses():
+    body = """
+    ld.global.nc.v2.u64 {%rd2, %rd3}, [%rd1];
+    ld.global.v8.f32 {%f0, %f1, %f2, %f3, %f4, %f5, %f6, %f7}, [%rd1+32];
+    st.global.b128 [%rd1], %q1;
+    atom.global.cas.b32 %r1, [%rd1], %r2, %r3;
+    ld.global.u32 %r4, [gv+4];
+    """
+    regs = ".reg .b64 %rd<8>;\n.reg .f32 %f<8>;\n.reg .b32 %r<8>;\n.reg .b128 %q<2>;"
+    src = HDR + ".global .align 8 .u32 gv[4];\n" + kernel(body, regs)[len(HDR):]
+    out, rep = ag.agile_guard_instrument_ptx(src, "sink")
+    assert [int(x[2]) for x in sites(out)] == [16, 32, 16, 4, 4]
+    assert "mov.u64 %__agd0, gv;" in out
+    assemble(out)
+
+
+@pytest.mark.parametrize("bad,code", [
+    ("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%rd1], [%rd2], 16, [%rd3];", -9),
+    ("cp.async.ca.shared.global [%rd1], [%rd2], 16;", -9),
+    ("st.async.b32 [%rd1], %r1, [%rd2];", -9),
+    ("multimem.ld_reduce.relaxed.sys.global.add.f32 %f1, [%rd1];", -9),
+    ("discard.global.L2 [%rd1], 128;", -9),
+])
+def test_uncoverable_forms_rejected(bad, code):
+    with pytest.raises(ag.AgileError) as e:
+        ag.agile_guard_instrument_ptx(kernel(bad), "poison")
+    assert e.value.code == code
+
+
+def test_rejects_guard_names_and_bad_modules():
+    out, _ = ag.agile_guard_instrument_ptx(STREAM, "poison")
+    with pytest.raises(ag.AgileError) as e:            # output cannot be fed back in
+        ag.agile_guard_instrument_ptx(out, "poison")
+    assert e.value.code == -9
+    with pytest.raises(ag.AgileError) as e:            # forging the table pointer
+        ag.agile_guard_instrument_ptx(HDR + ".global .u64 __agile_guard_table;\n", "poison")
+    assert e.value.code == -9
+    with pytest.raises(ag.AgileError) as e:
+        ag.agile_guard_instrument_ptx(".version 9.0\n.target sm_103a\n.address_size 32\n", "poison")
+    assert e.value.code == -9
+    with pytest.raises(ag.AgileError) as e:            # unbalanced body
+        ag.agile_guard_instrument_ptx(kernel("ld.global.f32 %f1, [%rd1];")[:-3], "poison")
+    assert e.value.code == -8
+
+
+def test_labels_comments_and_scopes():
+    body = """
+    // a comment with ld.global.f32 in it: not an access
+    /* block comment st.global.f32 [%rd1], %f1; */
+$L1:
+    {
+    .reg .f32 %ff;
+    ld.global.f32 %ff, [%rd1];   // inside a scope
+    }
+$L2: ld.global.f32 %f1, [%rd1+4];
+    """
+    out, rep = ag.agile_guard_instrument_ptx(kernel(body), "report")
+    assert rep["guarded"] == 2
+    assert "$L1:" in out and "$L2:" in out
+    assemble(out)
