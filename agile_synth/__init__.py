@@ -303,3 +303,86 @@ def stream_layout(n_elems: int, seed: int = SEED_BASE + 2, n_decoys: int = 1021,
     span = _round_up(need, 2 * MiB)
     r = layout(st, sizes, kinds, span, 0, min_gap=4 * KiB, align=align)
     return r, span, {name: find(r, 0x1000 + k) for k, name in enumerate("abc")}
+
+
+# ---------------------------------------------------------------- irregular access
+
+ODD_MIX = 0x9E3779B1          # odd: multiplication by it permutes residues mod 2^k
+
+
+def irregular_layout(n_idx: int, stripes: int = 4096, user_bytes: int = 4 * MiB,
+                     prot_bytes: int = 64 * KiB, bins: int = 1 << 20):
+    """Arena layout for gather / scatter / histogram: a table region of `stripes` user
+    allocations of `user_bytes`, each followed by a protected range of `prot_bytes`
+    (protected ranges interleaved through the table); a bins array (u32) followed by a
+    protected range; the int64 index array and the fp32 output array. Offsets are relative
+    to the arena start; all arrays are 256-byte aligned.
+
+    Returns (ranges_relative, arena_bytes, offsets {'t', 'bins', 'idx', 'out'}).
+    """
+    stripe = user_bytes + prot_bytes
+    base, size, kind, ident = [], [], [], []
+    for s in range(stripes):
+        base += [s * stripe, s * stripe + user_bytes]
+        size += [user_bytes, prot_bytes]
+        kind += [KIND_USER, KIND_PROTECTED]
+        ident += [0x20000 + s, 0x30000 + s]
+    cur = stripes * stripe + 64 * KiB
+    off = {"t": 0, "bins": cur}
+    base += [cur, cur + 4 * bins]
+    size += [4 * bins, prot_bytes]
+    kind += [KIND_USER, KIND_PROTECTED]
+    ident += [0x10, 0x11]
+    cur = _round_up(cur + 4 * bins + prot_bytes + 64 * KiB, 256)
+    off["idx"] = cur
+    base.append(cur); size.append(8 * n_idx); kind.append(KIND_USER); ident.append(0x12)
+    cur = _round_up(cur + 8 * n_idx + 64 * KiB, 256)
+    off["out"] = cur
+    base.append(cur); size.append(4 * n_idx); kind.append(KIND_USER); ident.append(0x13)
+    cur = _round_up(cur + 4 * n_idx + 64 * KiB, 2 * MiB)
+    return _ranges(base, size, kind, ident, stripes=stripes, user_bytes=user_bytes,
+                   prot_bytes=prot_bytes, bins=bins), cur, off
+
+
+def irregular_indices(n: int, stripes: int = 4096, user_bytes: int = 4 * MiB,
+                      prot_bytes: int = 64 * KiB, bins: int = 1 << 20, dist: str = "uniform",
+                      frac_bad: float = 0.001, seed: int = SEED_BASE + 3, chunk: int = 1 << 24):
+    """int64 element offsets into the table region and histogram keys into the bins.
+
+    A rank r is drawn over the user elements (uniform, or Zipf(1.1) with the rank mixed
+    by an odd multiplier modulo the user element count, a power of two, so hot elements
+    are spread over the table) and mapped to its stripe and position. Exactly
+    int(n * frac_bad) accesses, at random positions, are aimed into protected ranges
+    instead: a table index into a stripe's protected tail, and a key into the protected
+    range after the bins. Returns (idx, key, bad) with bad marking those positions.
+    """
+    st = Stream(seed, 9)
+    ue = user_bytes // 4
+    se = (user_bytes + prot_bytes) // 4
+    pe = prot_bytes // 4
+    total = stripes * ue
+    idx = np.empty(n, dtype=np.int64)
+    key = np.empty(n, dtype=np.int64)
+    for lo in range(0, n, chunk):
+        m = min(chunk, n - lo)
+        if dist == "uniform":
+            r = st.below(total, m)
+        elif dist == "zipf":
+            assert total & (total - 1) == 0, "Zipf mixing needs a power-of-two element count"
+            k = zipf(st, 1.1, total, m) - 1
+            r = ((k.astype(np.uint64) * U64(ODD_MIX)) & U64(total - 1)).astype(np.int64)
+        else:
+            raise ValueError(dist)
+        idx[lo:lo + m] = (r // ue) * se + r % ue
+        key[lo:lo + m] = r & (bins - 1)
+    nbad = int(n * frac_bad)
+    bad = np.zeros(n, dtype=bool)
+    if nbad:
+        pos = np.unique(st.below(n, nbad))
+        while len(pos) < nbad:                  # redraw the few collisions
+            pos = np.unique(np.concatenate([pos, st.below(n, nbad - len(pos))]))
+        bad[pos] = True
+        s_ = st.below(stripes, len(pos))
+        idx[pos] = s_ * se + ue + st.below(pe, len(pos))
+        key[pos] = bins + st.below(pe, len(pos))
+    return idx, key, bad

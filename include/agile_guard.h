@@ -212,6 +212,23 @@ AGILE_API int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *d
                         const float *d_c, size_t n, float s, int policy, void *d_log,
                         void *stream);
 
+enum { AGILE_IRR_GATHER = 0, AGILE_IRR_SCATTER = 1, AGILE_IRR_HIST = 2 };
+
+/* Irregular kernels with the guard fused in by hand (Sec. V-E), n elements, d_idx int64
+ * element offsets (16-byte aligned) that the kernel turns into addresses
+ * d_base + 4 * d_idx[i] -- the data-dependent addresses the guard exists for:
+ *   GATHER  d_out[i] = ((float *)d_base)[d_idx[i]]            (d_out 16-byte aligned)
+ *   SCATTER ((float *)d_base)[d_idx[i]] = (float)(d_idx[i] & 0xFFFFFF)
+ *   HIST    ((uint32_t *)d_base)[d_idx[i]] += 1 (atomic)
+ * Access order per group of four elements: two 16-byte index loads (sites 0, 1), the
+ * four element accesses (site 2), gather's 16-byte output store (site 3); elements past
+ * the last whole group use an 8-byte index load, the element access and a 4-byte store.
+ * Policies and tbl == NULL as for agile_stream_launch; under POISON a denied index load
+ * reads 0 and a denied element load reads 0.0f. */
+AGILE_API int agile_irregular_launch(int kind, const agile_dev_table_t *tbl, const int64_t *d_idx,
+                                     void *d_base, float *d_out, size_t n, int policy,
+                                     void *d_log, void *stream);
+
 /* ---------------------------------------------------------------- PTX guard pass */
 
 typedef struct {

@@ -150,3 +150,26 @@ def stream_plain(op: str, b: np.ndarray, c: np.ndarray | None, s: float = 3.0) -
     _L().orc_stream_plain(ctypes.c_int(STREAM_OPS[op]), ctypes.c_size_t(n), ctypes.c_float(s),
                           _p(b), _p(c), _p(a))
     return a
+
+
+IRREGULAR = {"gather": 0, "scatter": 1, "hist": 2}
+
+
+def irregular(kind: str, r, arena: np.ndarray, arena_va: int, va: dict, n: int,
+              policy: str = "poison"):
+    """Guarded gather / scatter / histogram over an arena copy (Sec. V-E guard and
+    policies; access order stated in agile_oracle.c). `arena` (uint8) is updated in
+    place; va: {'idx', 't', 'out'} guarded-space addresses. Returns the Log."""
+    base, size, kind_, ident = _table(r)
+    assert arena.dtype == np.uint8 and arena.flags.c_contiguous
+    log = _Log()
+    f = _L().orc_irregular
+    f.restype = ctypes.c_int
+    rc = f(ctypes.c_int(IRREGULAR[kind]), ctypes.c_size_t(n), ctypes.c_uint64(arena_va),
+           _p(arena), ctypes.c_size_t(len(arena)), ctypes.c_uint64(va["idx"]),
+           ctypes.c_uint64(va["t"]), ctypes.c_uint64(va.get("out", 0)),
+           ctypes.c_int(POLICY[policy]), ctypes.c_size_t(len(base)), _p(base), _p(size),
+           _p(kind_), _p(ident), ctypes.byref(log))
+    if rc != 0:
+        raise ValueError("an access that is carried out falls outside the arena")
+    return Log._of(log)

@@ -277,3 +277,91 @@ void orc_stream_plain(int op, size_t n, float s, const float *b, const float *c,
     for (size_t i = 0; i < n; ++i)
         a[i] = op == 0 ? b[i] : op == 1 ? s * b[i] : fmaf(s, c[i], b[i]);
 }
+
+/*
+ * Guarded irregular kernels over one arena (the caller's copy of the device memory that
+ * holds every array; arena_va is its address). Sec. V-E: each global access is checked
+ * first; the policy decides what a denied access does (as for the streaming kernels).
+ * Per unit u < n/4 of four elements:
+ *   site 0: 16-byte load of idx[4u], idx[4u+1];  site 1: 16-byte load of idx[4u+2..3]
+ *   site 2: for k = 0..3 the element access at T + 4*idx[4u+k] (4 bytes):
+ *           gather -- load; scatter -- store (float)(idx & 0xFFFFFF); hist -- atomic +1 (u32)
+ *   site 3: gather only -- 16-byte store of out[4u..4u+3]
+ * Tail elements i >= 4*(n/4): 8-byte idx load (site 0), the element access (site 2),
+ * gather's 4-byte out store (site 3). idx is int64; T + 4*idx wraps modulo 2^64.
+ * Returns 0, or -1 if an access that is carried out falls outside the arena.
+ */
+enum { IR_GATHER = 0, IR_SCATTER = 1, IR_HIST = 2 };
+
+typedef struct {
+    uint64_t va;
+    uint8_t *mem;
+    size_t len;
+} orc_arena;
+
+static int in_arena(const orc_arena *A, uint64_t a, uint64_t w) {
+    return a >= A->va && w <= A->len && a - A->va <= A->len - w;
+}
+
+/* One guarded access: classify, log a deny, and tell whether it is carried out. */
+static int guarded(const orc_sorted *s, orc_log *log, int policy, uint64_t a, uint64_t w,
+                   uint32_t site) {
+    uint32_t rid, v = classify_sorted(s, a, w, &rid);
+    if (v == V_ALLOW) return 1;
+    log_note(log, a, a, (uint32_t)w, v, site, rid);
+    return policy == P_REPORT;
+}
+
+int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t arena_len,
+                  uint64_t va_idx, uint64_t va_t, uint64_t va_out, int policy, size_t tn,
+                  const uint64_t *base, const uint64_t *size, const uint32_t *kindv,
+                  const uint32_t *id, orc_log *log) {
+    orc_table t = {tn, base, size, kindv, id};
+    orc_sorted *s = sorted_new(&t);
+    orc_arena A = {arena_va, arena, arena_len};
+    int rc = 0;
+    log_clear(log);
+    size_t units = n / 4, total = units + (n - 4 * units);
+    for (size_t u = 0; u < total && rc == 0; ++u) {
+        int vec = u < units;
+        size_t e0 = vec ? 4 * u : 4 * units + (u - units), cnt = vec ? 4 : 1;
+        int64_t idx[4] = {0, 0, 0, 0};
+        /* index loads */
+        for (size_t h = 0; h < (vec ? 2u : 1u); ++h) {
+            uint64_t a = va_idx + 8 * e0 + 16 * h, w = vec ? 16 : 8;
+            if (guarded(s, log, policy, a, w, (uint32_t)h)) {
+                if (!in_arena(&A, a, w)) { rc = -1; break; }
+                memcpy(idx + 2 * h, arena + (a - A.va), w);
+            }
+        }
+        /* element accesses */
+        float out[4] = {0, 0, 0, 0};
+        for (size_t k = 0; k < cnt && rc == 0; ++k) {
+            uint64_t a = va_t + 4 * (uint64_t)idx[k];
+            if (!guarded(s, log, policy, a, 4, 2)) continue;
+            if (!in_arena(&A, a, 4)) { rc = -1; break; }
+            uint8_t *p = arena + (a - A.va);
+            if (kind == IR_GATHER) {
+                memcpy(&out[k], p, 4);
+            } else if (kind == IR_SCATTER) {
+                float f = (float)((uint64_t)idx[k] & 0xFFFFFFu);
+                memcpy(p, &f, 4);
+            } else {
+                uint32_t c;
+                memcpy(&c, p, 4);
+                c += 1;
+                memcpy(p, &c, 4);
+            }
+        }
+        /* gather's output store */
+        if (kind == IR_GATHER && rc == 0) {
+            uint64_t a = va_out + 4 * e0, w = 4 * cnt;
+            if (guarded(s, log, policy, a, w, 3)) {
+                if (!in_arena(&A, a, w)) rc = -1;
+                else memcpy(arena + (a - A.va), out, w);
+            }
+        }
+    }
+    sorted_free(s);
+    return rc;
+}

@@ -21,6 +21,7 @@ VERDICTS = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID"]
 KINDS = {"user": 0, "protected": 1, "mmio": 2}
 POLICIES = {"poison": 0, "sink": 1, "report": 2, "trap": 3}
 OPS = {"copy": 0, "scale": 1, "triad": 2}
+IRREGULAR = {"gather": 0, "scatter": 1, "hist": 2}
 
 
 class AgileError(RuntimeError):
@@ -73,6 +74,8 @@ _SIG = {
     "agile_guard_check_batch": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
     "agile_stream_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
                                            ctypes.c_float, ctypes.c_int, _P, _P]),
+    "agile_irregular_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
+                                              ctypes.c_int, _P, _P]),
     "agile_guard_instrument_ptx": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, _P, _P, _P, _P]),
     "agile_module_load": (ctypes.c_int, [ctypes.c_char_p, _P]),
     "agile_module_bind": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -275,6 +278,14 @@ def agile_stream_launch(op: str, dev: DevTable | None, d_a, d_b, d_c, n: int, s:
     _check(lib().agile_stream_launch(OPS[op], dev.ref if dev is not None else None, _dptr(d_a),
                                      _dptr(d_b), _dptr(d_c), n, s, POLICIES[policy], _dptr(d_log),
                                      _stream(stream)), "agile_stream_launch")
+
+
+def agile_irregular_launch(kind: str, dev: DevTable | None, d_idx, d_base, d_out, n: int,
+                           policy: str = "poison", d_log=None, stream=None) -> None:
+    _check(lib().agile_irregular_launch(IRREGULAR[kind], dev.ref if dev is not None else None,
+                                        _dptr(d_idx), _dptr(d_base), _dptr(d_out), n,
+                                        POLICIES[policy], _dptr(d_log), _stream(stream)),
+           "agile_irregular_launch")
 
 
 # ---------------------------------------------------------------- PTX guard pass

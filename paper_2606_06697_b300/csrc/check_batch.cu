@@ -2,10 +2,11 @@
 // as the kernel guard of Sec. V-E applies it, with the first violation (smallest index)
 // and the violation count in the log.
 //
-// Launch shape: 512 threads, two blocks per SM, a warp-uniform grid-stride loop. Each lane
+// Launch shape: 512 threads, two blocks per SM, a grid-stride loop. Each lane
 // handles VEC consecutive accesses: VEC = 8 reads 64 address bytes as four 16-byte loads,
 // 8 width bytes as one 8-byte load and writes 8 verdict bytes as one 8-byte store. The
-// page map is staged into shared memory with one bulk copy when it fits.
+// page map is staged into shared memory with one bulk copy when it fits. Each thread keeps
+// its smallest violation in registers; the block reduces them once at the end.
 #include <cuda_runtime.h>
 
 #include "agile_internal.h"
@@ -46,10 +47,9 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
     const size_t ngroups = n / VEC;
 
-    for (size_t g0 = warp * 32; g0 < ngroups; g0 += nwarps * 32) {
-        const size_t g = g0 + lane;
-        LaneLog ll;
-        if (g < ngroups) {
+    LaneLog ll;
+    for (size_t g = warp * 32 + lane; g < ngroups; g += nwarps * 32) {
+        {
             if constexpr (VEC == 8) {
                 const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
                 uint4 q[4];
@@ -69,14 +69,12 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
                 verdict[g] = check_one(T, pg, __ldg(addr + g), __ldg(width + g), g, ll);
             }
         }
-        agile::warp_log(log, ll.cnt, ll.key, ll.info, ll.addr);
     }
     if (VEC > 1 && blockIdx.x == 0 && threadIdx.x < 32) {    // the last n % VEC accesses
         const size_t i = ngroups * VEC + lane;
-        LaneLog ll;
         if (i < n) verdict[i] = check_one(T, pg, __ldg(addr + i), __ldg(width + i), i, ll);
-        agile::warp_log(log, ll.cnt, ll.key, ll.info, ll.addr);
     }
+    agile::block_log_flush(log, ll);
 }
 
 template <bool SMEM, int VEC>

@@ -167,27 +167,6 @@ __device__ inline void cas_min128(unsigned long long *p, unsigned long long k,
     atomicOr(status, AGILE_LOG_STATUS_TIMEOUT);
 }
 
-// Warp-collective: every lane calls it. Lanes with cnt > 0 hold their smallest violation
-// (key, info, addr). One lane of the warp updates the log.
-__device__ inline void warp_log(LogDev *L, uint32_t cnt, unsigned long long key,
-                                unsigned long long info, unsigned long long addr) {
-    if (__ballot_sync(kFull, cnt != 0) == 0) return;
-    unsigned long long k = cnt ? key : ~0ull, v = cnt ? info : ~0ull, a = addr;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        unsigned long long k2 = __shfl_xor_sync(kFull, k, o);
-        unsigned long long v2 = __shfl_xor_sync(kFull, v, o);
-        unsigned long long a2 = __shfl_xor_sync(kFull, a, o);
-        if (k2 < k || (k2 == k && v2 < v)) { k = k2; v = v2; a = a2; }
-    }
-    uint32_t total = __reduce_add_sync(kFull, cnt);
-    if ((threadIdx.x & 31) == 0 && L != nullptr) {
-        atomicAdd(&L->count, (unsigned long long)total);
-        cas_min128(&L->first_key, k, v, &L->status);
-        cas_min128(&L->where_key, k, a, &L->status);
-    }
-}
-
 // Per-thread running minimum of the violations it has seen.
 struct LaneLog {
     uint32_t cnt = 0;
@@ -198,6 +177,46 @@ struct LaneLog {
         if (k < key || (k == key && i < info)) { key = k; info = i; addr = a; }
     }
 };
+
+__device__ __forceinline__ void min3_shfl(unsigned long long &k, unsigned long long &v,
+                                          unsigned long long &a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long k2 = __shfl_xor_sync(kFull, k, o);
+        unsigned long long v2 = __shfl_xor_sync(kFull, v, o);
+        unsigned long long a2 = __shfl_xor_sync(kFull, a, o);
+        if (k2 < k || (k2 == k && v2 < v)) { k = k2; v = v2; a = a2; }
+    }
+}
+
+// Block-collective, called once by every thread at the end of a kernel: the block's
+// violations are reduced to one count and one smallest record in shared memory, and one
+// thread updates the log. One global update per block keeps the log address cold.
+__device__ inline void block_log_flush(LogDev *L, const LaneLog &ll) {
+    __shared__ unsigned long long s_key[32], s_info[32], s_addr[32];
+    __shared__ uint32_t s_cnt[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long k = ll.cnt ? ll.key : ~0ull, v = ll.cnt ? ll.info : ~0ull, a = ll.addr;
+    min3_shfl(k, v, a);
+    uint32_t c = __reduce_add_sync(kFull, ll.cnt);
+    if (lane == 0) { s_key[warp] = k; s_info[warp] = v; s_addr[warp] = a; s_cnt[warp] = c; }
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t nw = (blockDim.x + 31) >> 5;
+        k = lane < nw ? s_key[lane] : ~0ull;
+        v = lane < nw ? s_info[lane] : ~0ull;
+        a = lane < nw ? s_addr[lane] : 0;
+        unsigned long long total = lane < nw ? s_cnt[lane] : 0;
+        min3_shfl(k, v, a);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
+        if (lane == 0 && total != 0 && L != nullptr) {
+            atomicAdd(&L->count, total);
+            cas_min128(&L->first_key, k, v, &L->status);
+            cas_min128(&L->where_key, k, a, &L->status);
+        }
+    }
+}
 
 // ------------------------------------------------------------------ page-map staging
 

@@ -49,18 +49,17 @@ __device__ __forceinline__ bool lane_check(const agile_dev_table_t &T, const uin
     return false;
 }
 
-// The per-lane path, out of line so the common path keeps few registers. Warp-collective:
-// called by all lanes when some unit k of this warp (bit k clear in `fast`) is not decided
-// by the warp-uniform check. Returns ok bits: bit 3k+0 b, 3k+1 c, 3k+2 a.
+// The per-lane path, out of line so the common path keeps few registers: called when some
+// unit k of this warp (bit k clear in `fast`) is not decided by the warp-uniform check.
+// Returns ok bits: bit 3k+0 b, 3k+1 c, 3k+2 a; violations go to the thread's LaneLog.
 template <int OP>
 __device__ __noinline__ uint32_t slow_units(const agile_dev_table_t &T, const uint32_t *pg,
                                             const float4 *a4, const float4 *b4, const float4 *c4,
                                             size_t first, size_t stride, size_t n4, uint32_t fast,
-                                            LogDev *log) {
+                                            LaneLog &ll) {
     constexpr bool kTriad = OP == AGILE_OP_TRIAD;
     constexpr uint32_t kSiteB = 0, kSiteC = 1, kSiteA = kTriad ? 2 : 1;
     uint32_t ok = ~0u;
-    LaneLog ll;
 #pragma unroll 1
     for (int k = 0; k < kUnroll; ++k) {
         const size_t i = first + k * stride;
@@ -69,7 +68,6 @@ __device__ __noinline__ uint32_t slow_units(const agile_dev_table_t &T, const ui
         if (kTriad && !lane_check(T, pg, (uint64_t)(c4 + i), 16, kSiteC, ll)) ok &= ~(2u << (3 * k));
         if (!lane_check(T, pg, (uint64_t)(a4 + i), 16, kSiteA, ll)) ok &= ~(4u << (3 * k));
     }
-    agile::warp_log(log, ll.cnt, ll.key, ll.info, ll.addr);
     return ok;
 }
 
@@ -97,6 +95,7 @@ k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restri
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t wbase = gtid - lane;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
+    LaneLog ll;
 
     for (size_t chunk = 0; chunk < n4; chunk += stride * kUnroll) {
         size_t idx[kUnroll];
@@ -119,7 +118,7 @@ k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restri
                 fast |= (uint32_t)f << k;
             }
             if (fast != (1u << kUnroll) - 1)
-                ok = slow_units<OP>(T, pg, a4, b4, c4, chunk + gtid, stride, n4, fast, log);
+                ok = slow_units<OP>(T, pg, a4, b4, c4, chunk + gtid, stride, n4, fast, ll);
         }
     float4 vb[kUnroll], vc[kUnroll];
 #pragma unroll
@@ -147,7 +146,6 @@ k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restri
         const size_t i = n4 * 4 + lane;
         const bool on = i < n;
         bool ob = true, oc = true, oa = true;
-        LaneLog ll;
         if constexpr (GUARD) {
             if (on) {
                 ob = lane_check(T, pg, (uint64_t)(b + i), 4, kSiteB, ll);
@@ -163,8 +161,8 @@ k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restri
             if (oa || kLoadAlways) a[i] = out;
             else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = out;
         }
-        if constexpr (GUARD) agile::warp_log(log, ll.cnt, ll.key, ll.info, ll.addr);
     }
+    if constexpr (GUARD) agile::block_log_flush(log, ll);
 }
 
 template <int OP, bool GUARD, bool SMEM, int POLICY>

@@ -93,3 +93,39 @@ def test_ptx_launch_refused_until_bound():
     with pytest.raises(ag.AgileError):
         ag.agile_module_launch(m, "no_such_kernel", 1, 32, [])
     m.unload()
+
+
+IRREGULAR = open(os.path.join(os.path.dirname(ag.library_path), "ptx", "irregular.ptx")).read()
+IRR_SITES = {"gather": [0, 1, 2, 2, 2, 2, 3, 0, 2, 3], "scatter": [0, 1, 2, 2, 2, 2, 0, 2],
+             "hist": [0, 1, 2, 2, 2, 2, 0, 2]}
+
+
+@pytest.mark.parametrize("policy", ["poison", "sink", "report"])
+@pytest.mark.parametrize("n", [7, 40_003])
+def test_ptx_irregular_parity(policy, n):
+    from test_gpu_irregular import put, setup
+    mod = ag.agile_module_load(ag.agile_guard_instrument_ptx(IRREGULAR, policy)[0])
+    try:
+        for kind in ("gather", "scatter", "hist"):
+            r, span, off, idx, key, bad, host, arena, base = setup(n, frac_bad=0.05)
+            put(host, off["idx"], key if kind == "hist" else idx)
+            t = r.shifted(base)
+            _, dev = device_table(t, 16)
+            arena.copy_(torch.from_numpy(host))
+            log = new_log(client=5)
+            ag.agile_module_bind(mod, dev, log)
+            target = off["bins"] if kind == "hist" else off["t"]
+            args = [ctypes.c_uint64(base + off["idx"]), ctypes.c_uint64(base + target),
+                    ctypes.c_uint64(base + off["out"]), ctypes.c_uint64(n)]
+            ag.agile_module_launch(mod, f"agile_ptx_{kind}", 148 * 2, 256, args)
+            rc, rec = ag.agile_violation_log_read(log)
+            va = {"t": base + target, "idx": base + off["idx"], "out": base + off["out"]}
+            olog = oracle.irregular(kind, t, host, base, va, n, policy)
+            assert (arena.cpu().numpy() == host).all(), kind
+            assert rec.count == olog.count and rec.client == 5
+            if olog.count:
+                assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
+                    (olog.key, olog.addr, olog.width, olog.verdict, olog.range_id), kind
+                assert IRR_SITES[kind][rec.site] == olog.site
+    finally:
+        mod.unload()

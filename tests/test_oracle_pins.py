@@ -281,3 +281,91 @@ def test_stream_guard_poison_protected_window():
     assert cross.sum() == 1          # the unit across byte 100 touches user and protected: PROTECTED
     got_r, log_r = oracle.stream("copy", t, va, b, None, np.zeros(n, np.float32), 1.0, "report")
     assert (got_r == b).all() and log_r == log
+
+
+# ---------------------------------------------------------------- irregular kernels
+
+
+def _irregular_case(n=4003, stripes=16, user=64 * 1024, prot=4 * 1024, bins=1 << 12,
+                    frac_bad=0.01, dist="uniform", base=0x7E0000000000):
+    r, span, off = syn.irregular_layout(n, stripes, user, prot, bins)
+    idx, key, bad = syn.irregular_indices(n, stripes, user, prot, bins, dist=dist,
+                                          frac_bad=frac_bad, seed=5)
+    arena = np.zeros(span, np.uint8)
+    st = syn.Stream(6, 6)
+    tvals = st.uniform((stripes * (user + prot)) // 4).astype(np.float32)
+    arena[:len(tvals) * 4] = tvals.view(np.uint8)
+    va = {"t": base + off["t"], "idx": base + off["idx"], "out": base + off["out"],
+          "bins": base + off["bins"]}
+    return r.shifted(base), arena, base, va, off, idx, key, bad, tvals
+
+
+def _put(arena, off, arr):
+    b = np.ascontiguousarray(arr).view(np.uint8)
+    arena[off:off + len(b)] = b
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+def test_irregular_gather_against_fancy_indexing(dist):
+    """Gather with no violation is T[idx]; with indices aimed into protected tails,
+    poison gives 0.0 there, report gives the tail's contents, and the log counts them."""
+    t, arena, base, va, off, idx, key, bad, tvals = _irregular_case(dist=dist)
+    n = len(idx)
+    _put(arena, off["idx"], idx)
+    for policy in ("poison", "sink", "report"):
+        a = arena.copy()
+        log = oracle.irregular("gather", t, a, base, va, n, policy)
+        got = a[off["out"]:off["out"] + 4 * n].view(np.float32)
+        want = tvals[idx]
+        if policy != "report":
+            want = np.where(bad, np.float32(0), want)
+        assert (got == want).all()
+        assert log.count == int(bad.sum())
+        first = int(va["t"] + 4 * idx[bad].min())
+        assert (log.key, log.addr, log.site, log.width, log.verdict) == (first, first, 2, 4, 1)
+
+
+def test_irregular_scatter_and_hist_against_numpy():
+    t, arena, base, va, off, idx, key, bad, tvals = _irregular_case()
+    n = len(idx)
+    _put(arena, off["idx"], idx)
+    a = arena.copy()
+    log = oracle.irregular("scatter", t, a, base, va, n, "poison")
+    T = a[:len(tvals) * 4].view(np.float32)
+    want = tvals.copy()
+    want[idx[~bad]] = (idx[~bad] & 0xFFFFFF).astype(np.float32)
+    assert (T == want).all() and log.count == int(bad.sum())
+    # histogram: the key array stands in for idx, the bins for the table
+    va_h = {"t": va["bins"], "idx": va["idx"]}
+    a = arena.copy()
+    _put(a, off["idx"], key)
+    log = oracle.irregular("hist", t, a, base, va_h, n, "poison")
+    bins = a[off["bins"]:off["bins"] + 4 * (1 << 12)].view(np.uint32)
+    assert (bins == np.bincount(key[~bad], minlength=1 << 12)).all()
+    assert log.count == int(bad.sum())
+    a = arena.copy()
+    _put(a, off["idx"], key)
+    oracle.irregular("hist", t, a, base, va_h, n, "report")
+    tail = a[off["bins"] + 4 * (1 << 12):off["bins"] + 4 * (1 << 12) + 4096].view(np.uint32)
+    assert tail.sum() == int(bad.sum())          # report lets the denied increments land
+
+
+def test_irregular_denied_index_load_reads_zero():
+    """A protected range laid over part of the index array: under poison those index
+    loads read 0, so the elements they feed gather T[0]."""
+    t, arena, base, va, off, idx, key, bad, tvals = _irregular_case(frac_bad=0)
+    n = len(idx)
+    _put(arena, off["idx"], idx)
+    # carve [32, 96) bytes of the idx array out as protected (two 16-byte loads, units 1-2)
+    ranges = [(int(b), int(s), int(k), int(i)) for b, s, k, i in zip(t.base, t.size, t.kind, t.ident)]
+    ix = next(j for j, x in enumerate(ranges) if x[3] == 0x12)
+    b0, s0, _, _ = ranges.pop(ix)
+    ranges += [(b0, 32, 0, 0x12), (b0 + 32, 64, 1, 0x99), (b0 + 96, s0 - 96, 0, 0x98)]
+    t2 = syn._ranges(*zip(*ranges))
+    a = arena.copy()
+    log = oracle.irregular("gather", t2, a, base, va, n, "poison")
+    got = a[off["out"]:off["out"] + 4 * n].view(np.float32)
+    want = tvals[idx].copy()
+    want[4:12] = tvals[0]
+    assert (got == want).all()
+    assert log.count == 4 and (log.key, log.site, log.width, log.range_id) == (b0 + 32, 0, 16, 0x99)
