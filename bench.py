@@ -392,22 +392,24 @@ def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):
     return out
 
 
-def batch_throughput(ag, torch, dev, stream):
+def batch_throughput(ag, torch, dev, stream, sizes=(1 << 20, 1 << 28), reps=None):
     t = syn.batch_table()
     tbl = ag.agile_guard_table_build(t.base, t.size, t.kind, t.ident, 21)
     buf = torch.empty(tbl.device_bytes(), dtype=torch.uint8, device=dev)
     dtab = tbl.upload(buf, stream)
     log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
     out = {}
-    for name, n in (("1M", 1 << 20), ("2^28", 1 << 28)):
-        addr, width, _ = syn.batch_accesses(t, 1 << 20)
-        da = torch.from_numpy(addr.view(np.int64)).to(dev).repeat(n // (1 << 20))
-        dw = torch.from_numpy(width).to(dev).repeat(n // (1 << 20))
+    for n in sizes:
+        name = f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)
+        m = min(n, 1 << 20)
+        addr, width, _ = syn.batch_accesses(t, m)
+        da = torch.from_numpy(addr.view(np.int64)).to(dev).repeat((n + m - 1) // m)[:n]
+        dw = torch.from_numpy(width).to(dev).repeat((n + m - 1) // m)[:n]
         dv = torch.empty(n, dtype=torch.uint8, device=dev)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-        reps = 20 if n == 1 << 20 else 5
+        nrep = reps or (20 if n <= 1 << 20 else 5)
         tot = 0.0
-        for i in range(reps + 3):
+        for i in range(nrep + 3):
             flush.fill_(i & 0xFF)                          # evict the inputs from L2
             ag.agile_violation_log_init(log, 0, stream)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -419,7 +421,7 @@ def batch_throughput(ag, torch, dev, stream):
             torch.cuda.synchronize()
             if i >= 3:
                 tot += e0.elapsed_time(e1)
-        ms = tot / reps
+        ms = tot / nrep
         out[name] = {"checks_per_s": n / (ms / 1e3), "ms": ms,
                      "gbs": n * 10 / (ms / 1e3) / 1e9, "bytes_per_check": 10}
         del da, dw, dv, flush
@@ -436,6 +438,8 @@ def main():
                     help="elements per array (the workload is 2^28; smaller only for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="guarded steps only: no unguarded, PTX, batch, e2e or CPU legs")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="N",
+                    help="only time the batch check on N accesses (profiling)")
     args = ap.parse_args()
     global N_ELEMS, STEP_BYTES
     N_ELEMS = args.elements - args.elements % 4
@@ -446,6 +450,14 @@ def main():
                       int(os.environ.get("RANK", "0")))
         return
     ws, rank, local = dist_setup()
+    if args.batch_only:
+        import torch
+        import paper_2606_06697_b300 as ag
+        torch.cuda.set_device(local)
+        st = torch.cuda.Stream()
+        print(json.dumps({"batch_check": batch_throughput(ag, torch, f"cuda:{local}", st,
+                                                          sizes=(args.batch_only,), reps=args.steps)}))
+        return
     run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist

@@ -60,77 +60,103 @@ __host__ __device__ inline unsigned long long pack_info(uint32_t site, uint32_t 
 
 // ------------------------------------------------------------------ classification
 
+// The table as a kernel sees it: pointers into shared memory (staged copies) or global.
+struct TView {
+    uint64_t lo, npages;
+    uint32_t lg, n;
+    const uint32_t *page;
+    const uint64_t *base, *end;
+    const uint32_t *kind, *id;
+};
+
+__device__ __forceinline__ TView view_of(const agile_dev_table_t &T) {
+    return TView{T.lo, T.npages, T.log2_page, T.n, T.page, T.base, T.end, T.kind, T.id};
+}
+
 __device__ __forceinline__ uint32_t deny_of_kind(uint32_t kind) {
     return kind == AGILE_MMIO ? AGILE_DENY_MMIO
          : kind == AGILE_PROTECTED ? AGILE_DENY_PROTECTED : AGILE_DENY_STRADDLE;
 }
 
-// Search ranges [lo_i, hi_i) for the last one starting at or below a, then walk.
-static __device__ __noinline__ uint32_t classify_search(const agile_dev_table_t &T, uint32_t lo_i,
-                                                 uint32_t hi_i, uint64_t a, uint64_t w,
-                                                 uint32_t *rid) {
+// Search ranges [lo_i, hi_i) for the last one starting at or below a, then walk the
+// ranges [a, a + w) touches in address order.
+__device__ __forceinline__ uint32_t search(const TView &V, uint32_t lo_i, uint32_t hi_i,
+                                          uint64_t a, uint64_t w, uint32_t *rid) {
     uint32_t b = lo_i, len = hi_i - lo_i;
     while (len > 0) {                       // b = first index in [lo_i, hi_i) with base > a
-        uint32_t half = len >> 1;
-        bool le = __ldg(T.base + b + half) <= a;
+        const uint32_t half = len >> 1;
+        const bool le = V.base[b + half] <= a;
         b = le ? b + half + 1 : b;
         len = le ? len - half - 1 : half;
     }
     uint32_t first = b;
     if (b > lo_i) {
-        uint32_t j = b - 1;
-        uint64_t e = __ldg(T.end + j);
+        const uint32_t j = b - 1;
+        const uint64_t e = V.end[j];
         if (e > a) {
-            if (__ldg(T.kind + j) == AGILE_USER && a + w <= e) {
-                *rid = __ldg(T.id + j);
-                return AGILE_ALLOW;
-            }
+            if (V.kind[j] == AGILE_USER && a + w <= e) { *rid = V.id[j]; return AGILE_ALLOW; }
             first = j;
         }
     }
     uint32_t best = 3, bj = 0;              // rank: 0 MMIO, 1 PROTECTED, 2 USER
-    for (uint32_t k = first; k < T.n; ++k) {
-        if (__ldg(T.base + k) >= a + w) break;
-        uint32_t kd = __ldg(T.kind + k);
-        uint32_t r = kd == AGILE_MMIO ? 0u : kd == AGILE_PROTECTED ? 1u : 2u;
+    for (uint32_t k = first; k < V.n; ++k) {
+        if (V.base[k] >= a + w) break;
+        const uint32_t kd = V.kind[k];
+        const uint32_t r = kd == AGILE_MMIO ? 0u : kd == AGILE_PROTECTED ? 1u : 2u;
         if (r < best) { best = r; bj = k; }
     }
     if (best == 3) { *rid = kNoRange; return AGILE_DENY_UNMAPPED; }
-    *rid = __ldg(T.id + bj);
+    *rid = V.id[bj];
     return best == 0 ? AGILE_DENY_MMIO : best == 1 ? AGILE_DENY_PROTECTED : AGILE_DENY_STRADDLE;
 }
 
-// Verdict of [a, a + w) for 1 <= w; pg is the page map (shared or global memory).
-__device__ __forceinline__ uint32_t classify(const agile_dev_table_t &T, const uint32_t *pg,
-                                             uint64_t a, uint64_t w, uint32_t *rid) {
+// Verdict of [a, a + w), w >= 1 any size, fully inline.
+__device__ __forceinline__ uint32_t classify(const TView &V, uint64_t a, uint64_t w, uint32_t *rid) {
     if (w == 0 || a > ~0ull - w) { *rid = kNoRange; return AGILE_DENY_INVALID; }
-    uint64_t off = a - T.lo;
-    uint64_t p = off >> T.log2_page;
-    uint32_t lo_i = 0, hi_i = T.n;
-    if (p < T.npages) {
-        uint32_t e = pg[p];
-        uint32_t f = e & kIdxMask, ty = e >> 30;
-        uint64_t G = 1ull << T.log2_page;
+    const uint64_t off = a - V.lo;
+    const uint64_t p = off >> V.lg;
+    uint32_t lo_i = 0, hi_i = V.n;
+    if (p < V.npages) {
+        const uint32_t e = V.page[p];
+        const uint32_t f = e & kIdxMask, ty = e >> 30;
+        const uint64_t G = 1ull << V.lg;
         if ((off & (G - 1)) + w <= G) {
             if (ty == PG_USER) { *rid = kNoRange; return AGILE_ALLOW; }
             if (ty == PG_HOLE) { *rid = kNoRange; return AGILE_DENY_UNMAPPED; }
-            if (ty == PG_DENY) { *rid = __ldg(T.id + f); return deny_of_kind(__ldg(T.kind + f)); }
+            if (ty == PG_DENY) { *rid = V.id[f]; return deny_of_kind(V.kind[f]); }
         }
-        uint32_t f2 = pg[p + 1] & kIdxMask;
+        const uint32_t f2 = V.page[p + 1] & kIdxMask;
         lo_i = f;
-        hi_i = f2 + 1 < T.n ? f2 + 1 : T.n;
+        hi_i = f2 + 1 < V.n ? f2 + 1 : V.n;
     }
-    return classify_search(T, lo_i, hi_i, a, w, rid);
+    return search(V, lo_i, hi_i, a, w, rid);
 }
 
-// True when [a, a + bytes) lies inside one USER page: every access inside it is allowed.
-__device__ __forceinline__ bool span_in_user_page(const agile_dev_table_t &T, const uint32_t *pg,
-                                                  uint64_t a, uint64_t bytes) {
-    uint64_t off = a - T.lo;
-    uint64_t p = off >> T.log2_page;
-    if (p >= T.npages) return false;
-    uint64_t G = 1ull << T.log2_page;
-    return (pg[p] >> 30) == PG_USER && (off & (G - 1)) + bytes <= G;
+// Out-of-line form for paths where the common case is decided elsewhere.
+static __device__ __noinline__ uint32_t classify_slow(const TView &V, uint64_t a, uint64_t w, uint32_t *rid) {
+    return classify(V, a, w, rid);
+}
+
+// Page of a byte, or ~0u outside the window.
+__device__ __forceinline__ uint32_t page_entry(const TView &V, uint64_t a) {
+    const uint64_t p = (a - V.lo) >> V.lg;
+    return p < V.npages ? V.page[p] : ~0u;
+}
+
+// [a, a + bytes) lies inside one user allocation when the pages of its first and last
+// byte are both all-user pages of the same range: the range is an interval holding
+// both. Inline, two page reads; false means "not decided here".
+__device__ __forceinline__ bool span_fast(const TView &V, uint64_t a, uint64_t bytes) {
+    const uint32_t e0 = page_entry(V, a), e1 = page_entry(V, a + bytes - 1);
+    return (e0 >> 30) == PG_USER && e0 == e1;
+}
+
+// Whole-span check: the fast test, else the full classification of the span as one
+// access (allowed iff inside one user allocation).
+__device__ __forceinline__ bool span_allowed(const TView &V, uint64_t a, uint64_t bytes) {
+    if (span_fast(V, a, bytes)) return true;
+    uint32_t rid;
+    return classify_slow(V, a, bytes, &rid) == AGILE_ALLOW;
 }
 
 // ------------------------------------------------------------------ violation log
@@ -248,31 +274,134 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-// Copy the page map into shared memory with one bulk copy (TMA, non-multicast) completed
-// on an mbarrier. Every thread of the block calls it. Returns the map to use: the shared
-// copy, or -- if the wait gave up -- the global one (results stay exact; the log, when
-// present, is flagged).
-__device__ inline const uint32_t *stage_page_map(const agile_dev_table_t &T, uint32_t *s_page,
-                                                 unsigned long long *s_bar, LogDev *log) {
-    uint32_t bytes = (uint32_t)(((T.npages + 1) * 4 + 15) & ~15ull);
-    uint32_t bar = smem_addr(s_bar);
+// Shared-memory staging modes chosen by the host: nothing, the page map, or the page map
+// and the range arrays.
+enum : int { STAGE_NONE = 0, STAGE_PAGES = 1, STAGE_ALL = 2 };
+
+__host__ __device__ inline uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
+
+// Bytes of shared memory a staging mode needs for table T.
+__host__ __device__ inline uint32_t stage_bytes(const agile_dev_table_t &T, int mode) {
+    if (mode == STAGE_NONE) return 0;
+    uint32_t b = round16((T.npages + 1) * 4);
+    if (mode == STAGE_ALL) b += 2 * round16(T.n * 8ull) + 2 * round16(T.n * 4ull);
+    return b;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Copy the table sections the mode asks for into shared memory with bulk copies (TMA,
+// non-multicast) completed on one mbarrier; every thread of the block calls it and
+// waits (bounded). Sections in the device buffer are 256-byte aligned and padded, so
+// 16-byte rounded copies stay inside them. If the wait gives up, the thread copies the
+// sections with plain loads instead (results stay exact) and the log, when present, is
+// flagged.
+template <int MODE>
+__device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *smem,
+                                    unsigned long long *s_bar, LogDev *log) {
+    TView V = view_of(T);
+    if constexpr (MODE == STAGE_NONE) return V;
+    const uint32_t pb = round16((T.npages + 1) * 4);
+    const uint32_t bb = round16(T.n * 8ull), kb = round16(T.n * 4ull);
+    uint32_t *s_page = reinterpret_cast<uint32_t *>(smem);
+    uint64_t *s_base = reinterpret_cast<uint64_t *>(smem + pb);
+    uint64_t *s_end = reinterpret_cast<uint64_t *>(smem + pb + bb);
+    uint32_t *s_kind = reinterpret_cast<uint32_t *>(smem + pb + 2 * bb);
+    uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + pb + 2 * bb + kb);
+    const uint32_t bar = smem_addr(s_bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+        const uint32_t total = MODE == STAGE_ALL ? pb + 2 * bb + 2 * kb : pb;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total)
                      : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-            ::"r"(smem_addr(s_page)), "l"(T.page), "r"(bytes), "r"(bar)
-            : "memory");
+        bulk_g2s(s_page, T.page, pb, bar);
+        if (MODE == STAGE_ALL && T.n > 0) {
+            bulk_g2s(s_base, T.base, bb, bar);
+            bulk_g2s(s_end, T.end, bb, bar);
+            bulk_g2s(s_kind, T.kind, kb, bar);
+            bulk_g2s(s_id, T.id, kb, bar);
+        }
     }
-    if (mbar_wait(bar, 0)) return s_page;
-    if (log != nullptr && threadIdx.x == 0) atomicOr(&log->status, AGILE_LOG_STATUS_TIMEOUT);
-    mbar_wait(bar, 0);                      // let the copy in flight land before moving on
-    return T.page;
+    if (!mbar_wait(bar, 0)) {               // (block-uniform only by timing: any thread may)
+        if (log != nullptr && threadIdx.x == 0) atomicOr(&log->status, AGILE_LOG_STATUS_TIMEOUT);
+        mbar_wait(bar, 0);                  // let copies in flight land, then copy by hand:
+        for (uint32_t i = threadIdx.x; i < pb / 4; i += blockDim.x) s_page[i] = T.page[i];
+        if (MODE == STAGE_ALL)              // identical bytes, so a late bulk write is harmless
+            for (uint32_t i = threadIdx.x; i < T.n; i += blockDim.x) {
+                s_base[i] = T.base[i]; s_end[i] = T.end[i]; s_kind[i] = T.kind[i]; s_id[i] = T.id[i];
+            }
+    }
+    __syncthreads();
+    V.page = s_page;
+    if constexpr (MODE == STAGE_ALL) {
+        V.base = s_base; V.end = s_end; V.kind = s_kind; V.id = s_id;
+    }
+    return V;
+}
+
+// Per-warp violation slots in shared memory, written only by slow paths.
+struct WarpSlots {
+    unsigned long long key[32], info[32], addr[32];
+    uint32_t cnt[32];
+};
+
+__device__ inline void slots_init(WarpSlots &S) {
+    if (threadIdx.x < 32) {
+        S.key[threadIdx.x] = ~0ull; S.info[threadIdx.x] = ~0ull;
+        S.addr[threadIdx.x] = 0; S.cnt[threadIdx.x] = 0;
+    }
+}
+
+// Warp-collective: fold every lane's LaneLog into this warp's slot.
+__device__ inline void warp_note(WarpSlots &S, const LaneLog &ll) {
+    unsigned long long k = ll.cnt ? ll.key : ~0ull, v = ll.cnt ? ll.info : ~0ull, a = ll.addr;
+    min3_shfl(k, v, a);
+    const uint32_t c = __reduce_add_sync(kFull, ll.cnt);
+    const uint32_t w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0 && c) {
+        S.cnt[w] += c;
+        if (k < S.key[w] || (k == S.key[w] && v < S.info[w])) {
+            S.key[w] = k; S.info[w] = v; S.addr[w] = a;
+        }
+    }
+    __syncwarp();
+}
+
+// Block-collective at kernel end: reduce the warp slots, one log update per block.
+__device__ inline void slots_flush(LogDev *L, WarpSlots &S) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x, nw = (blockDim.x + 31) >> 5;
+        unsigned long long k = lane < nw ? S.key[lane] : ~0ull;
+        unsigned long long v = lane < nw ? S.info[lane] : ~0ull;
+        unsigned long long a = lane < nw ? S.addr[lane] : 0;
+        unsigned long long total = lane < nw ? S.cnt[lane] : 0;
+        min3_shfl(k, v, a);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
+        if (lane == 0 && total != 0 && L != nullptr) {
+            atomicAdd(&L->count, total);
+            cas_min128(&L->first_key, k, v, &L->status);
+            cas_min128(&L->where_key, k, a, &L->status);
+        }
+    }
+}
+
+// Host side: pick the staging mode for a table (96 KiB for everything, 48 KiB for pages).
+inline int stage_mode(const agile_dev_table_t &T, bool want_ranges) {
+    if (T.npages == 0) return STAGE_NONE;
+    if (want_ranges && stage_bytes(T, STAGE_ALL) <= 96 * 1024) return STAGE_ALL;
+    if (stage_bytes(T, STAGE_PAGES) <= 48 * 1024) return STAGE_PAGES;
+    return STAGE_NONE;
 }
 
 }  // namespace agile

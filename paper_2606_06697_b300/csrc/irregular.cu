@@ -7,7 +7,8 @@
 // 16-byte loads (sites 0 and 1) and output stored as one 16-byte store (site 3), both
 // contiguous across the warp, so one warp-uniform page check decides them; the four
 // element accesses (site 2) go to data-dependent addresses and are checked per lane --
-// a shared-memory page-map lookup, and a binary search only on mixed pages. The n mod 4
+// a page-map lookup, and a binary search only on mixed pages, on a shared-memory copy of
+// the table when it fits (the page map alone otherwise). The n mod 4
 // tail elements use an 8-byte index load, the element access and a 4-byte store.
 #include <cuda_runtime.h>
 
@@ -18,14 +19,14 @@ namespace {
 
 using agile::LaneLog;
 using agile::LogDev;
+using agile::TView;
 
 constexpr int kThreads = 512;
-constexpr uint32_t kSmemMax = 48 * 1024;
 
-__device__ __forceinline__ bool lane_check(const agile_dev_table_t &T, const uint32_t *pg,
-                                           uint64_t a, uint32_t w, uint32_t site, LaneLog &ll) {
+__device__ __forceinline__ bool lane_check(const TView &V, uint64_t a, uint32_t w, uint32_t site,
+                                           LaneLog &ll) {
     uint32_t rid;
-    uint32_t v = agile::classify(T, pg, a, w, &rid);
+    uint32_t v = agile::classify(V, a, w, &rid);
     if (v == AGILE_ALLOW) return true;
     ll.note(a, agile::pack_info(site, v, w, rid), a);
     return false;
@@ -49,14 +50,14 @@ __device__ __forceinline__ float element(float *addr, bool ok, int64_t e, const 
     }
 }
 
-template <int KIND, bool GUARD, bool SMEM, int POLICY>
+template <int KIND, bool GUARD, int MODE, int POLICY>
 __global__ void __launch_bounds__(kThreads, 2)
 k_irregular(const agile_dev_table_t T, const int64_t *__restrict__ idx, float *base,
             float *__restrict__ out, size_t n, LogDev *log) {
-    extern __shared__ __align__(16) uint32_t s_page[];
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_bar;
-    const uint32_t *pg = T.page;
-    if constexpr (GUARD && SMEM) pg = agile::stage_page_map(T, s_page, &s_bar, log);
+    TView V{};
+    if constexpr (GUARD) V = agile::stage_table<MODE>(T, smem, &s_bar, log);
     constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
     constexpr bool kGather = KIND == AGILE_IRR_GATHER;
 
@@ -77,14 +78,14 @@ k_irregular(const agile_dev_table_t T, const int64_t *__restrict__ idx, float *b
         bool ok0 = true, ok1 = true, oko = true;
         if constexpr (GUARD) {
             const bool full = u0 + 32 <= n4;
-            const bool fast_i = full && agile::span_in_user_page(T, pg, (uint64_t)(idx2 + 2 * u0), 1024);
+            const bool fast_i = full && agile::span_allowed(V, (uint64_t)(idx2 + 2 * u0), 1024);
             if (!fast_i && act) {
-                ok0 = lane_check(T, pg, (uint64_t)(idx2 + 2 * u), 16, 0, ll);
-                ok1 = lane_check(T, pg, (uint64_t)(idx2 + 2 * u + 1), 16, 1, ll);
+                ok0 = lane_check(V, (uint64_t)(idx2 + 2 * u), 16, 0, ll);
+                ok1 = lane_check(V, (uint64_t)(idx2 + 2 * u + 1), 16, 1, ll);
             }
             if constexpr (kGather) {
-                const bool fast_o = full && agile::span_in_user_page(T, pg, (uint64_t)(out4 + u0), 512);
-                if (!fast_o && act) oko = lane_check(T, pg, (uint64_t)(out4 + u), 16, 3, ll);
+                const bool fast_o = full && agile::span_allowed(V, (uint64_t)(out4 + u0), 512);
+                if (!fast_o && act) oko = lane_check(V, (uint64_t)(out4 + u), 16, 3, ll);
             }
         }
         if (!act) continue;                  // no collective below: lanes may leave
@@ -95,7 +96,7 @@ k_irregular(const agile_dev_table_t T, const int64_t *__restrict__ idx, float *b
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float *addr = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e[k]);
-            const bool ok = !GUARD || lane_check(T, pg, (uint64_t)addr, 4, 2, ll);
+            const bool ok = !GUARD || lane_check(V, (uint64_t)addr, 4, 2, ll);
             v[k] = element<KIND, POLICY>(addr, ok, e[k], T);
         }
         if constexpr (kGather) {
@@ -108,13 +109,13 @@ k_irregular(const agile_dev_table_t T, const int64_t *__restrict__ idx, float *b
     if (blockIdx.x == 0 && threadIdx.x < 32 && (n & 3)) {          // tail elements
         const size_t i = n4 * 4 + lane;
         if (i < n) {
-            const bool oki = !GUARD || lane_check(T, pg, (uint64_t)(idx + i), 8, 0, ll);
+            const bool oki = !GUARD || lane_check(V, (uint64_t)(idx + i), 8, 0, ll);
             const int64_t e = *((oki || kAlways) ? idx + i : reinterpret_cast<const int64_t *>(T.zero_page));
             float *addr = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e);
-            const bool ok = !GUARD || lane_check(T, pg, (uint64_t)addr, 4, 2, ll);
+            const bool ok = !GUARD || lane_check(V, (uint64_t)addr, 4, 2, ll);
             const float v = element<KIND, POLICY>(addr, ok, e, T);
             if constexpr (kGather) {
-                const bool oko = !GUARD || lane_check(T, pg, (uint64_t)(out + i), 4, 3, ll);
+                const bool oko = !GUARD || lane_check(V, (uint64_t)(out + i), 4, 3, ll);
                 if (oko || kAlways) out[i] = v;
                 else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = v;
             }
@@ -123,16 +124,31 @@ k_irregular(const agile_dev_table_t T, const int64_t *__restrict__ idx, float *b
     if constexpr (GUARD) agile::block_log_flush(log, ll);
 }
 
-template <int KIND, bool GUARD, bool SMEM, int POLICY>
+template <int KIND, bool GUARD, int MODE, int POLICY>
 int launch(const agile_dev_table_t &T, const int64_t *idx, void *base, float *out, size_t n,
-           LogDev *log, cudaStream_t st, uint32_t smem) {
+           LogDev *log, cudaStream_t st) {
+    const uint32_t smem = GUARD ? agile::stage_bytes(T, MODE) : 0;
+    if (smem > 48 * 1024) {
+        AGILE_CUDA_TRY(cudaFuncSetAttribute(k_irregular<KIND, GUARD, MODE, POLICY>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    }
     size_t want = ((n >> 2) + kThreads - 1) / kThreads;
     size_t cap = (size_t)agile::sm_count() * 2;
     unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
-    k_irregular<KIND, GUARD, SMEM, POLICY><<<blocks, kThreads, (GUARD && SMEM) ? smem : 0, st>>>(
+    k_irregular<KIND, GUARD, MODE, POLICY><<<blocks, kThreads, smem, st>>>(
         T, idx, reinterpret_cast<float *>(base), out, n, log);
     AGILE_CUDA_TRY(cudaGetLastError());
     return AGILE_OK;
+}
+
+template <int KIND, int POLICY>
+int by_mode(const agile_dev_table_t &T, const int64_t *idx, void *base, float *out, size_t n,
+            LogDev *log, cudaStream_t st) {
+    switch (agile::stage_mode(T, true)) {
+        case agile::STAGE_ALL: return launch<KIND, true, agile::STAGE_ALL, POLICY>(T, idx, base, out, n, log, st);
+        case agile::STAGE_PAGES: return launch<KIND, true, agile::STAGE_PAGES, POLICY>(T, idx, base, out, n, log, st);
+        default: return launch<KIND, true, agile::STAGE_NONE, POLICY>(T, idx, base, out, n, log, st);
+    }
 }
 
 template <int KIND>
@@ -140,23 +156,13 @@ int dispatch(const agile_dev_table_t *tbl, const int64_t *idx, void *base, float
              int policy, LogDev *log, cudaStream_t st) {
     if (tbl == nullptr) {
         agile_dev_table_t none = {};
-        return launch<KIND, false, false, AGILE_POLICY_REPORT>(none, idx, base, out, n, nullptr, st, 0);
+        return launch<KIND, false, agile::STAGE_NONE, AGILE_POLICY_REPORT>(none, idx, base, out, n, nullptr, st);
     }
-    const uint64_t map_bytes = ((tbl->npages + 1) * 4 + 15) & ~15ull;
-    const bool smem = tbl->npages > 0 && map_bytes <= kSmemMax;
-    const uint32_t sb = (uint32_t)map_bytes;
     switch (policy) {
-        case AGILE_POLICY_POISON:
-            return smem ? launch<KIND, true, true, AGILE_POLICY_POISON>(*tbl, idx, base, out, n, log, st, sb)
-                        : launch<KIND, true, false, AGILE_POLICY_POISON>(*tbl, idx, base, out, n, log, st, 0);
-        case AGILE_POLICY_SINK:
-            return smem ? launch<KIND, true, true, AGILE_POLICY_SINK>(*tbl, idx, base, out, n, log, st, sb)
-                        : launch<KIND, true, false, AGILE_POLICY_SINK>(*tbl, idx, base, out, n, log, st, 0);
-        case AGILE_POLICY_REPORT:
-            return smem ? launch<KIND, true, true, AGILE_POLICY_REPORT>(*tbl, idx, base, out, n, log, st, sb)
-                        : launch<KIND, true, false, AGILE_POLICY_REPORT>(*tbl, idx, base, out, n, log, st, 0);
-        default:
-            return AGILE_ERR_INVALID_ARG;
+        case AGILE_POLICY_POISON: return by_mode<KIND, AGILE_POLICY_POISON>(*tbl, idx, base, out, n, log, st);
+        case AGILE_POLICY_SINK: return by_mode<KIND, AGILE_POLICY_SINK>(*tbl, idx, base, out, n, log, st);
+        case AGILE_POLICY_REPORT: return by_mode<KIND, AGILE_POLICY_REPORT>(*tbl, idx, base, out, n, log, st);
+        default: return AGILE_ERR_INVALID_ARG;
     }
 }
 

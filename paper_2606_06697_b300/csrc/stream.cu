@@ -3,13 +3,16 @@
 // address-range check before every global access, ordinary user-allocation accesses left
 // on the normal path), and their unguarded twins.
 //
-// Guard placement. A warp's k-th unit covers 32 consecutive 16-byte vectors, i.e. one
-// contiguous 512-byte span per array. When that span lies inside one all-user page of the
-// map, every access in it is allowed: one shared-memory broadcast read decides the whole
-// warp (the warp-uniform fast path). Otherwise each lane classifies its own access and
-// the policy applies per access: POISON and SINK redirect denied loads to the table's
-// zero page; POISON drops denied stores, SINK sends them to the sink page; REPORT lets
-// every access through. Denied accesses are logged with key (address, site).
+// Guard placement. Work is cut into warp tiles of 128 16-byte units (2 KiB per array);
+// lane l handles units l, l+32, l+64, l+96, so every access is coalesced. Before a tile,
+// the warp checks each array's 2 KiB span once: if the pages of its first and last byte
+// are all-user pages of the same allocation, the whole span lies inside that allocation
+// and every access in it is allowed; otherwise the span is classified as one access.
+// Only when a span is not allowed does the warp take the per-access path (out of line),
+// where each lane classifies its own accesses and the policy applies: POISON and SINK
+// send denied loads to the table's zero page; POISON drops denied stores, SINK sends
+// them to the sink page; REPORT lets every access through. Denied accesses are logged
+// with key (address, site) into per-warp shared-memory slots, reduced once per block.
 #include <cuda_runtime.h>
 
 #include "agile_internal.h"
@@ -19,10 +22,12 @@ namespace {
 
 using agile::LaneLog;
 using agile::LogDev;
+using agile::TView;
+using agile::WarpSlots;
 
 constexpr int kThreads = 512;
-constexpr int kUnroll = 4;
-constexpr uint32_t kSmemMax = 48 * 1024;
+constexpr int kU = 4;                        // units per lane per tile
+constexpr uint32_t kTileUnits = 32 * kU;     // 128 units = 2 KiB per array
 
 template <int OP>
 __device__ __forceinline__ float4 op4(float s, float4 b, float4 c) {
@@ -39,143 +44,154 @@ __device__ __forceinline__ float op1(float s, float b, float c) {
     return __fmaf_rn(s, c, b);
 }
 
-// Per-lane check of one access; notes a violation. Returns whether it is allowed.
-__device__ __forceinline__ bool lane_check(const agile_dev_table_t &T, const uint32_t *pg,
-                                           uint64_t a, uint32_t w, uint32_t site, LaneLog &ll) {
+__device__ __forceinline__ bool lane_ok(const TView &V, uint64_t a, uint32_t w, uint32_t site,
+                                        LaneLog &ll) {
     uint32_t rid;
-    uint32_t v = agile::classify(T, pg, a, w, &rid);
+    const uint32_t v = agile::classify(V, a, w, &rid);
     if (v == AGILE_ALLOW) return true;
     ll.note(a, agile::pack_info(site, v, w, rid), a);
     return false;
 }
 
-// The per-lane path, out of line so the common path keeps few registers: called when some
-// unit k of this warp (bit k clear in `fast`) is not decided by the warp-uniform check.
-// Returns ok bits: bit 3k+0 b, 3k+1 c, 3k+2 a; violations go to the thread's LaneLog.
-template <int OP>
-__device__ __noinline__ uint32_t slow_units(const agile_dev_table_t &T, const uint32_t *pg,
-                                            const float4 *a4, const float4 *b4, const float4 *c4,
-                                            size_t first, size_t stride, size_t n4, uint32_t fast,
-                                            LaneLog &ll) {
+// Per-access path for one warp tile (units u0 .. u0+127 clipped to n4; for the n mod 4
+// tail, the lane's element is 4*n4 + lane with 4-byte accesses). Warp-collective.
+// Applies the policy and logs into the warp's slot.
+template <int OP, int POLICY, bool TAIL>
+__device__ __noinline__ void slow_tile(const TView &V, const agile_dev_table_t &T, float *a,
+                                       const float *b, const float *c, size_t u0, size_t n4,
+                                       size_t n, float s, WarpSlots &S) {
     constexpr bool kTriad = OP == AGILE_OP_TRIAD;
     constexpr uint32_t kSiteB = 0, kSiteC = 1, kSiteA = kTriad ? 2 : 1;
-    uint32_t ok = ~0u;
+    constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
+    const uint32_t lane = threadIdx.x & 31;
+    LaneLog ll;
+    if constexpr (!TAIL) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(b);
+        const float4 *c4 = reinterpret_cast<const float4 *>(c);
+        float4 *a4 = reinterpret_cast<float4 *>(a);
+        const float4 *zero4 = reinterpret_cast<const float4 *>(T.zero_page);
 #pragma unroll 1
-    for (int k = 0; k < kUnroll; ++k) {
-        const size_t i = first + k * stride;
-        if ((fast >> k) & 1 || i >= n4) continue;
-        if (!lane_check(T, pg, (uint64_t)(b4 + i), 16, kSiteB, ll)) ok &= ~(1u << (3 * k));
-        if (kTriad && !lane_check(T, pg, (uint64_t)(c4 + i), 16, kSiteC, ll)) ok &= ~(2u << (3 * k));
-        if (!lane_check(T, pg, (uint64_t)(a4 + i), 16, kSiteA, ll)) ok &= ~(4u << (3 * k));
+        for (int k = 0; k < kU; ++k) {
+            const size_t u = u0 + 32 * k + lane;
+            if (u >= n4) continue;
+            const bool okb = lane_ok(V, (uint64_t)(b4 + u), 16, kSiteB, ll);
+            const bool okc = !kTriad || lane_ok(V, (uint64_t)(c4 + u), 16, kSiteC, ll);
+            const bool oka = lane_ok(V, (uint64_t)(a4 + u), 16, kSiteA, ll);
+            const float4 vb = __ldcs((okb || kAlways) ? b4 + u : zero4);
+            const float4 vc = kTriad ? __ldcs((okc || kAlways) ? c4 + u : zero4) : vb;
+            const float4 o = op4<OP>(s, vb, vc);
+            if (oka || kAlways) __stcs(a4 + u, o);
+            else if constexpr (POLICY == AGILE_POLICY_SINK) __stcs(reinterpret_cast<float4 *>(T.sink_page), o);
+        }
+    } else {
+        const size_t i = 4 * n4 + lane;
+        if (i < n) {
+            const float *zero = reinterpret_cast<const float *>(T.zero_page);
+            const bool okb = lane_ok(V, (uint64_t)(b + i), 4, kSiteB, ll);
+            const bool okc = !kTriad || lane_ok(V, (uint64_t)(c + i), 4, kSiteC, ll);
+            const bool oka = lane_ok(V, (uint64_t)(a + i), 4, kSiteA, ll);
+            const float vb = *((okb || kAlways) ? b + i : zero);
+            const float vc = kTriad ? *((okc || kAlways) ? c + i : zero) : 0.f;
+            const float o = op1<OP>(s, vb, vc);
+            if (oka || kAlways) a[i] = o;
+            else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = o;
+        }
     }
-    return ok;
+    agile::warp_note(S, ll);
 }
 
-template <int OP, bool GUARD, bool SMEM, int POLICY>
+template <int OP, bool GUARD, int MODE, int POLICY>
 __global__ void __launch_bounds__(kThreads, 2)
 k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restrict__ b,
          const float *__restrict__ c, size_t n, float s, LogDev *log) {
-    extern __shared__ __align__(16) uint32_t s_page[];
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_bar;
-    const uint32_t *pg = T.page;
-    if constexpr (GUARD && SMEM) pg = agile::stage_page_map(T, s_page, &s_bar, log);
-
+    __shared__ WarpSlots S;
     constexpr bool kTriad = OP == AGILE_OP_TRIAD;
-    constexpr uint32_t kSiteB = 0, kSiteC = 1, kSiteA = kTriad ? 2 : 1;
-    constexpr bool kLoadAlways = POLICY == AGILE_POLICY_REPORT;
+    TView V{};
+    if constexpr (GUARD) {
+        agile::slots_init(S);
+        __syncthreads();
+        V = agile::stage_table<MODE>(T, smem, &s_bar, log);
+    }
 
     const size_t n4 = n >> 2;
     const float4 *b4 = reinterpret_cast<const float4 *>(b);
     const float4 *c4 = reinterpret_cast<const float4 *>(c);
     float4 *a4 = reinterpret_cast<float4 *>(a);
-    const float4 *zero4 = reinterpret_cast<const float4 *>(T.zero_page);
-    float4 *sink4 = reinterpret_cast<float4 *>(T.sink_page);
-
     const uint32_t lane = threadIdx.x & 31;
-    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t wbase = gtid - lane;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    LaneLog ll;
+    const size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const size_t full_tiles = n4 / kTileUnits;
+    const size_t tiles = (n4 + kTileUnits - 1) / kTileUnits;
 
-    for (size_t chunk = 0; chunk < n4; chunk += stride * kUnroll) {
-        size_t idx[kUnroll];
-        bool act[kUnroll];
-        uint32_t ok = ~0u;                  // bit 3k+0 b, 3k+1 c, 3k+2 a
-#pragma unroll
-        for (int k = 0; k < kUnroll; ++k) {
-            idx[k] = chunk + k * stride + gtid;
-            act[k] = idx[k] < n4;
-        }
+    for (size_t t = warp; t < tiles; t += nwarps) {          // warp-uniform
+        const size_t u0 = t * kTileUnits;
+        bool fast = t < full_tiles;
         if constexpr (GUARD) {
-            uint32_t fast = 0;              // warp-uniform
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                const size_t w0 = chunk + k * stride + wbase;
-                bool f = w0 + 32 <= n4 &&
-                         agile::span_in_user_page(T, pg, (uint64_t)(b4 + w0), 512) &&
-                         agile::span_in_user_page(T, pg, (uint64_t)(a4 + w0), 512);
-                if constexpr (kTriad) f = f && agile::span_in_user_page(T, pg, (uint64_t)(c4 + w0), 512);
-                fast |= (uint32_t)f << k;
+            fast = fast && agile::span_allowed(V, (uint64_t)(b4 + u0), 16 * kTileUnits) &&
+                   agile::span_allowed(V, (uint64_t)(a4 + u0), 16 * kTileUnits);
+            if constexpr (kTriad)
+                fast = fast && agile::span_allowed(V, (uint64_t)(c4 + u0), 16 * kTileUnits);
+            if (!fast) {
+                slow_tile<OP, POLICY, false>(V, T, a, b, c, u0, n4, n, s, S);
+                continue;
             }
-            if (fast != (1u << kUnroll) - 1)
-                ok = slow_units<OP>(T, pg, a4, b4, c4, chunk + gtid, stride, n4, fast, ll);
-        }
-    float4 vb[kUnroll], vc[kUnroll];
+        } else if (!fast) {                                   // unguarded partial tile
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) {
-            if (act[k]) {
-                const bool okb = (ok >> (3 * k)) & 1, okc = (ok >> (3 * k + 1)) & 1;
-                vb[k] = __ldcs((okb || kLoadAlways) ? b4 + idx[k] : zero4);
-                if constexpr (kTriad) vc[k] = __ldcs((okc || kLoadAlways) ? c4 + idx[k] : zero4);
-                else vc[k] = vb[k];
+            for (int k = 0; k < kU; ++k) {
+                const size_t u = u0 + 32 * k + lane;
+                if (u < n4) __stcs(a4 + u, op4<OP>(s, __ldcs(b4 + u), kTriad ? __ldcs(c4 + u) : float4{}));
             }
+            continue;
+        }
+        float4 vb[kU], vc[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            vb[k] = __ldcs(b4 + u0 + 32 * k + lane);
+            if constexpr (kTriad) vc[k] = __ldcs(c4 + u0 + 32 * k + lane);
+            else vc[k] = vb[k];
         }
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) {
-            if (act[k]) {
-                float4 out = op4<OP>(s, vb[k], vc[k]);
-                const bool oka = (ok >> (3 * k + 2)) & 1;
-                if (oka || kLoadAlways) __stcs(a4 + idx[k], out);
-                else if constexpr (POLICY == AGILE_POLICY_SINK) __stcs(sink4, out);
-            }
-        }
+        for (int k = 0; k < kU; ++k) __stcs(a4 + u0 + 32 * k + lane, op4<OP>(s, vb[k], vc[k]));
     }
 
-    // Elements past the last whole 16-byte unit: 4-byte accesses, same sites and policy.
-    if (blockIdx.x == 0 && threadIdx.x < 32 && (n & 3)) {
-        const size_t i = n4 * 4 + lane;
-        const bool on = i < n;
-        bool ob = true, oc = true, oa = true;
+    // Elements past the last whole 16-byte unit: 4-byte accesses by the last warp.
+    if ((n & 3) && blockIdx.x == gridDim.x - 1 && (threadIdx.x >> 5) == (blockDim.x >> 5) - 1) {
         if constexpr (GUARD) {
-            if (on) {
-                ob = lane_check(T, pg, (uint64_t)(b + i), 4, kSiteB, ll);
-                if constexpr (kTriad) oc = lane_check(T, pg, (uint64_t)(c + i), 4, kSiteC, ll);
-                oa = lane_check(T, pg, (uint64_t)(a + i), 4, kSiteA, ll);
-            }
-        }
-        if (on) {
-            const float *zero = reinterpret_cast<const float *>(T.zero_page);
-            float vb1 = *((ob || kLoadAlways) ? b + i : zero);
-            float vc1 = kTriad ? *((oc || kLoadAlways) ? c + i : zero) : 0.f;
-            float out = op1<OP>(s, vb1, vc1);
-            if (oa || kLoadAlways) a[i] = out;
-            else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = out;
+            slow_tile<OP, POLICY, true>(V, T, a, b, c, n4, n4, n, s, S);
+        } else {
+            const size_t i = 4 * n4 + lane;
+            if (i < n) a[i] = op1<OP>(s, b[i], kTriad ? c[i] : 0.f);
         }
     }
-    if constexpr (GUARD) agile::block_log_flush(log, ll);
+    if constexpr (GUARD) agile::slots_flush(log, S);
 }
 
-template <int OP, bool GUARD, bool SMEM, int POLICY>
+template <int OP, bool GUARD, int MODE, int POLICY>
 int launch(const agile_dev_table_t &T, float *a, const float *b, const float *c, size_t n,
-           float s, LogDev *log, cudaStream_t st, uint32_t smem) {
-    size_t n4 = n >> 2;
-    size_t want = (n4 + kThreads - 1) / kThreads;
-    size_t cap = (size_t)agile::sm_count() * 2;
-    unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
-    k_stream<OP, GUARD, SMEM, POLICY><<<blocks, kThreads, (GUARD && SMEM) ? smem : 0, st>>>(
-        T, a, b, c, n, s, log);
+           float s, LogDev *log, cudaStream_t st) {
+    const uint32_t smem = GUARD ? agile::stage_bytes(T, MODE) : 0;
+    if (smem > 48 * 1024) {
+        AGILE_CUDA_TRY(cudaFuncSetAttribute(k_stream<OP, GUARD, MODE, POLICY>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    }
+    const size_t tiles = ((n >> 2) + kTileUnits - 1) / kTileUnits;
+    const size_t want = (tiles * 32 + kThreads - 1) / kThreads;
+    const size_t cap = (size_t)agile::sm_count() * 2;
+    const unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
+    k_stream<OP, GUARD, MODE, POLICY><<<blocks, kThreads, smem, st>>>(T, a, b, c, n, s, log);
     AGILE_CUDA_TRY(cudaGetLastError());
     return AGILE_OK;
+}
+
+template <int OP, int POLICY>
+int by_mode(const agile_dev_table_t &T, float *a, const float *b, const float *c, size_t n,
+            float s, LogDev *log, cudaStream_t st) {
+    switch (agile::stage_mode(T, false)) {
+        case agile::STAGE_PAGES: return launch<OP, true, agile::STAGE_PAGES, POLICY>(T, a, b, c, n, s, log, st);
+        default: return launch<OP, true, agile::STAGE_NONE, POLICY>(T, a, b, c, n, s, log, st);
+    }
 }
 
 template <int OP>
@@ -183,23 +199,13 @@ int dispatch(const agile_dev_table_t *tbl, float *a, const float *b, const float
              float s, int policy, LogDev *log, cudaStream_t st) {
     if (tbl == nullptr) {
         agile_dev_table_t none = {};
-        return launch<OP, false, false, AGILE_POLICY_REPORT>(none, a, b, c, n, s, nullptr, st, 0);
+        return launch<OP, false, agile::STAGE_NONE, AGILE_POLICY_REPORT>(none, a, b, c, n, s, nullptr, st);
     }
-    const uint64_t map_bytes = ((tbl->npages + 1) * 4 + 15) & ~15ull;
-    const bool smem = tbl->npages > 0 && map_bytes <= kSmemMax;
-    const uint32_t sb = (uint32_t)map_bytes;
     switch (policy) {
-        case AGILE_POLICY_POISON:
-            return smem ? launch<OP, true, true, AGILE_POLICY_POISON>(*tbl, a, b, c, n, s, log, st, sb)
-                        : launch<OP, true, false, AGILE_POLICY_POISON>(*tbl, a, b, c, n, s, log, st, 0);
-        case AGILE_POLICY_SINK:
-            return smem ? launch<OP, true, true, AGILE_POLICY_SINK>(*tbl, a, b, c, n, s, log, st, sb)
-                        : launch<OP, true, false, AGILE_POLICY_SINK>(*tbl, a, b, c, n, s, log, st, 0);
-        case AGILE_POLICY_REPORT:
-            return smem ? launch<OP, true, true, AGILE_POLICY_REPORT>(*tbl, a, b, c, n, s, log, st, sb)
-                        : launch<OP, true, false, AGILE_POLICY_REPORT>(*tbl, a, b, c, n, s, log, st, 0);
-        default:
-            return AGILE_ERR_INVALID_ARG;
+        case AGILE_POLICY_POISON: return by_mode<OP, AGILE_POLICY_POISON>(*tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_SINK: return by_mode<OP, AGILE_POLICY_SINK>(*tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_REPORT: return by_mode<OP, AGILE_POLICY_REPORT>(*tbl, a, b, c, n, s, log, st);
+        default: return AGILE_ERR_INVALID_ARG;
     }
 }
 
