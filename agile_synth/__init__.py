@@ -386,3 +386,76 @@ def irregular_indices(n: int, stripes: int = 4096, user_bytes: int = 4 * MiB,
         idx[pos] = s_ * se + ue + st.below(pe, len(pos))
         key[pos] = bins + st.below(pe, len(pos))
     return idx, key, bad
+
+
+# ---------------------------------------------------------------- many clients
+
+def lognormal(stream: Stream, median: float, sigma: float, n: int) -> np.ndarray:
+    """Lognormal draws (Box-Muller normals, float64)."""
+    u1 = stream.uniform(n) * (1 - 1e-12) + 1e-12
+    u2 = stream.uniform(n)
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2 * np.pi * u2)
+    return median * np.exp(sigma * z)
+
+
+def client_specs(n_clients: int = 256, seed: int = SEED_BASE + 4, median: int = 2 * MiB,
+                 sigma: float = float(np.log(128) / 3), lo: int = 4 * KiB, hi: int = 256 * MiB,
+                 table_lo: int = 8, table_hi: int = 4096, mix=(0.5, 0.3, 0.2)):
+    """Per-client kernel kind (copy / gather / hist in the given mix), buffer size
+    (lognormal, clamped to [lo, hi], 256-byte multiple) and table size (log-uniform)."""
+    st = Stream(seed, 11)
+    counts = [int(round(m * n_clients)) for m in mix]
+    counts[0] += n_clients - sum(counts)
+    ops = np.array(["copy"] * counts[0] + ["gather"] * counts[1] + ["hist"] * counts[2])
+    ops = ops[st.permutation(n_clients)]
+    size = np.clip(lognormal(st, median, sigma, n_clients), lo, hi).astype(np.int64) // 256 * 256
+    ranges = st.log_uniform(table_lo, table_hi, n_clients)
+    return [{"client": i, "op": str(ops[i]), "bytes": int(size[i]), "ranges": int(ranges[i])}
+            for i in range(n_clients)]
+
+
+HIST_BINS = 1 << 14
+
+
+def client_buffers(spec: dict):
+    """Buffers a client's kernel uses: name -> bytes, and its element count n."""
+    B = spec["bytes"]
+    if spec["op"] == "copy":
+        return {"a": B, "b": B}, B // 4
+    if spec["op"] == "gather":
+        n = max(B // 16, 1)
+        return {"t": B, "idx": 8 * n, "out": 4 * n}, n
+    n = max(B // 8, 1)
+    return {"bins": 4 * HIST_BINS, "idx": 8 * n}, n
+
+
+def client_layout(spec: dict, seed: int = SEED_BASE + 4):
+    """A client's arena: its buffers as user allocations plus decoy allocations (user,
+    protected, MMIO; 4-64 KiB) up to its table size, every range surrounded by holes.
+    Returns (ranges_relative, arena_bytes, {buffer: offset}, n)."""
+    st = Stream(seed, 100 + spec["client"])
+    bufs, n = client_buffers(spec)
+    names = list(bufs)
+    nd = max(spec["ranges"] - len(names), 0)
+    dsize = st.log_uniform(4 * KiB, 64 * KiB, nd)
+    u = st.uniform(nd)
+    dkind = np.where(u < 0.9, KIND_USER, np.where(u < 0.98, KIND_PROTECTED, KIND_MMIO))
+    sizes = np.concatenate([[bufs[k] for k in names], dsize]).astype(np.int64)
+    kinds = np.concatenate([[KIND_USER] * len(names), dkind])
+    span = _round_up(int(_round_up(sizes, 256).sum()) + (len(sizes) + 1) * 8 * KiB, 2 * MiB)
+    r = layout(st, sizes, kinds, span, 0, min_gap=4 * KiB, align=256)
+    return r, span, {k: find(r, 0x1000 + i) for i, k in enumerate(names)}, n
+
+
+def client_indices(spec: dict, n: int, seed: int = SEED_BASE + 4, frac_bad: float = 0.0,
+                   bad_target: int | None = None):
+    """Gather offsets (uniform over the table's elements) or histogram keys (uniform over
+    the bins); int(n * frac_bad) of them, at random positions, are replaced by the element
+    offset `bad_target` (an address the caller picked outside the client's user ranges)."""
+    st = Stream(seed, 200 + spec["client"])
+    hi = spec["bytes"] // 4 if spec["op"] == "gather" else HIST_BINS
+    idx = st.below(hi, n)
+    nbad = int(n * frac_bad)
+    if nbad and bad_target is not None:
+        idx[np.unique(st.below(n, nbad))] = bad_target
+    return idx

@@ -305,6 +305,7 @@ def run_ours(args, ws, rank, local):
 
     # batch check throughput: the 1M-access table workload and a 2^28-access stream
     batch = batch_throughput(ag, torch, dev, stream)
+    clients = batch_clients(ag, torch, dev, stream)
 
     # end to end through host buffers: H2D of b, c, the three guarded kernels, D2H of a
     e2e_steps = max(3, min(args.steps // 100, 10))
@@ -356,7 +357,7 @@ def run_ours(args, ws, rank, local):
             "ptx_injected_gbs": ptx_gbs, "ptx_injected_kernel_ms": ptx_kern,
             "kernel_ms": {f"{op}_guarded": kern[op] for op in ops} |
                          {f"{op}_unguarded": kern_u[op] for op in ops},
-            "roofline": roofline, "batch_check": batch, "e2e": e2e,
+            "roofline": roofline, "batch_check": batch, "batch_clients": clients, "e2e": e2e,
             "gpu_launches": args.steps * 4, "clocks": ck, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -390,6 +391,54 @@ def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):
     assert rc == 0 and rec.count == 0, "violation in the PTX-injected run"
     mod.unload()
     return out
+
+
+def batch_clients(ag, torch, dev, stream, n_clients=256, reps=5):
+    """256 clients (50% copy, 30% gather, 20% histogram; lognormal buffers, median 2 MiB;
+    tables of 8-4096 ranges): one persistent guarded launch (autotuned, then replayed as a
+    CUDA graph) against 256 separate guarded launches."""
+    from paper_2606_06697_b300.clients import ClientSet
+    specs = syn.client_specs(n_clients)
+    cs = ClientSet(specs, dev, log2_pages=(16, 21))
+    n = len(cs.clients)
+    buf = torch.empty(ag.agile_batch_device_bytes(n), dtype=torch.uint8, device=dev)
+    best = ag.agile_batch_autotune([cs.work(0), cs.work(1)], [4096, 16384, 65536, 262144], buf,
+                                   reps=3, stream=stream)
+    v = best["variant"]
+    ag.agile_batch_upload(cs.work(v), best["tile"], buf, stream)
+    nbytes = cs.algorithmic_bytes()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        out = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    def separate():
+        for i in range(n):
+            cs.run_single(i, v, stream=stream)
+
+    def batched():
+        ag.agile_batch_launch(buf, n, best["tile"], best["span_checks"], best["blocks_per_sm"], stream)
+
+    g = ag.agile_batch_graph_create(buf, n, best["tile"], best["span_checks"], best["blocks_per_sm"])
+    ms_sep = timed(separate)
+    ms_bat = timed(batched)
+    ms_graph = timed(lambda: g.launch(stream))
+    g.destroy()
+    return {"clients": n, "algorithmic_bytes": nbytes, "tuned": best,
+            "separate_launches_ms": ms_sep, "batched_ms": ms_bat, "graph_replay_ms": ms_graph,
+            "separate_gbs": nbytes / ms_sep / 1e6, "graph_gbs": nbytes / ms_graph / 1e6,
+            "speedup_graph_vs_separate": ms_sep / ms_graph,
+            "mix": {o: sum(1 for s_ in specs if s_["op"] == o) for o in ("copy", "gather", "hist")}}
 
 
 def batch_throughput(ag, torch, dev, stream, sizes=(1 << 20, 1 << 28), reps=None):

@@ -113,6 +113,8 @@ typedef struct {
     void *zero_page;          /* 64 zero bytes read by denied loads under SINK           */
     void *sink_page;          /* 64 bytes that take denied stores under SINK             */
     uint64_t bytes;           /* size of the device buffer in use                       */
+    uint32_t search_steps;    /* binary-search steps that cover any page's range slice  */
+    uint32_t reserved;
 } agile_dev_table_t;
 
 /* Decoded violation log. The first fault is the violating access with the smallest
@@ -228,6 +230,89 @@ enum { AGILE_IRR_GATHER = 0, AGILE_IRR_SCATTER = 1, AGILE_IRR_HIST = 2 };
 AGILE_API int agile_irregular_launch(int kind, const agile_dev_table_t *tbl, const int64_t *d_idx,
                                      void *d_base, float *d_out, size_t n, int policy,
                                      void *d_log, void *stream);
+
+/* ---------------------------------------------------------------- batched clients */
+
+/* Kinds of work a batch item runs: the streaming and irregular kernels above. */
+enum {
+    AGILE_WORK_COPY = 0, AGILE_WORK_SCALE = 1, AGILE_WORK_TRIAD = 2,
+    AGILE_WORK_GATHER = 3, AGILE_WORK_SCATTER = 4, AGILE_WORK_HIST = 5
+};
+
+/* One client's guarded kernel inside a batch (64 bytes). Streaming kinds: out = a,
+ * in0 = b, in1 = c (TRIAD only), s the scalar. Irregular kinds: in0 = int64 offsets,
+ * in1 = the table or bins base, out = gather's output. `table` is the device address of
+ * the client's uploaded table buffer (256-byte aligned; NULL runs the item unguarded),
+ * `log` the client's violation log (may be NULL). Alignment as for the single launches. */
+typedef struct {
+    uint32_t op;
+    uint32_t policy;
+    uint64_t n;
+    const void *table;
+    void *log;
+    void *out;
+    const void *in0;
+    const void *in1;
+    float s;
+    uint32_t client;
+} agile_work_t;
+
+/* Launch shape of a batch. */
+typedef struct {
+    uint32_t tile;            /* elements per tile, a multiple of 512                      */
+    uint32_t span_checks;     /* 1: one check per contiguous warp span; 0: every access    */
+    uint32_t blocks_per_sm;   /* 1 or 2 resident 512-thread blocks per SM                  */
+    uint32_t reserved;        /* set by the library                                        */
+} agile_batch_config_t;
+
+/* Result of agile_batch_autotune. */
+typedef struct {
+    agile_batch_config_t config;
+    uint32_t variant;         /* which of the work-list variants won (e.g. page size)      */
+    uint32_t cached;          /* 1 when read from the cache file                          */
+    float ms;                 /* mean time of one launch                                   */
+} agile_batch_tuning_t;
+
+/* A captured, instantiated CUDA graph (opaque). */
+typedef struct agile_graph agile_graph_t;
+
+/* Device bytes of a batch buffer for up to max_items work items. */
+AGILE_API size_t agile_batch_device_bytes(size_t max_items);
+
+/* Check the n work items (INVALID_ARG / ALIGN as the single launches would) and copy
+ * them, with their tile prefix sums for `tile`, into the caller-owned d_buf (256-byte
+ * aligned, >= agile_batch_device_bytes(n)). Synchronous on `stream`. */
+AGILE_API int agile_batch_upload(const agile_work_t *h_items, size_t n, uint32_t tile,
+                                 void *d_buf, size_t bytes, void *stream);
+
+/* Run an uploaded batch as one persistent launch (Sec. IV-B: one worker runs the CUDA
+ * operations of many clients; Sec. V-E: each client's kernel guarded by its own table,
+ * logging into its own log). Blocks claim tiles from a counter in d_buf, which this
+ * call resets first (a memset, then the kernel, on `stream`). n_items must match the
+ * upload. Each client's outputs and log equal those of its single launch. */
+AGILE_API int agile_batch_launch(void *d_buf, size_t n_items, const agile_batch_config_t *cfg,
+                                 void *stream);
+
+/* Capture agile_batch_launch(d_buf, n_items, cfg) into a CUDA graph and instantiate it.
+ * Replays read the work list in d_buf at replay time, so re-uploading a list of the same
+ * length (and tile) and replaying runs the new list. */
+AGILE_API int agile_batch_graph_create(void *d_buf, size_t n_items, const agile_batch_config_t *cfg,
+                                       agile_graph_t **out);
+AGILE_API int agile_graph_launch(agile_graph_t *g, void *stream);
+AGILE_API void agile_graph_destroy(agile_graph_t *g);
+
+/* Pick the fastest launch for a batch: every variant (n_variants work lists of n_items
+ * each, back to back in h_variants -- e.g. the same work with tables of different page
+ * sizes) x every candidate tile x span checks on/off x 1 or 2 blocks per SM, timed with
+ * CUDA events over `reps` launches after one warm-up. The items really run: outputs of
+ * non-idempotent kinds (HIST) and the logs must be reset afterwards. With cache_path,
+ * a result keyed by the items' kinds and sizes is read from / appended to that file.
+ * The winning variant is left uploaded only if it was the last one tried; upload it
+ * again before launching. */
+AGILE_API int agile_batch_autotune(const agile_work_t *h_variants, size_t n_variants,
+                                   size_t n_items, const uint32_t *tiles, size_t n_tiles,
+                                   void *d_buf, size_t bytes, int reps, const char *cache_path,
+                                   void *stream, agile_batch_tuning_t *best);
 
 /* ---------------------------------------------------------------- PTX guard pass */
 

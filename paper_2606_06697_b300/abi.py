@@ -22,6 +22,7 @@ KINDS = {"user": 0, "protected": 1, "mmio": 2}
 POLICIES = {"poison": 0, "sink": 1, "report": 2, "trap": 3}
 OPS = {"copy": 0, "scale": 1, "triad": 2}
 IRREGULAR = {"gather": 0, "scatter": 1, "hist": 2}
+WORK = {"copy": 0, "scale": 1, "triad": 2, "gather": 3, "scatter": 4, "hist": 5}
 
 
 class AgileError(RuntimeError):
@@ -51,6 +52,24 @@ class _Record(ctypes.Structure):
                 ("status", ctypes.c_uint32), ("count", ctypes.c_uint64)]
 
 
+class Work(ctypes.Structure):
+    """agile_work_t: one client's guarded kernel inside a batch."""
+    _fields_ = [("op", ctypes.c_uint32), ("policy", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("table", ctypes.c_void_p), ("log", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("in0", ctypes.c_void_p), ("in1", ctypes.c_void_p), ("s", ctypes.c_float),
+                ("client", ctypes.c_uint32)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_uint32), ("span_checks", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("config", BatchConfig), ("variant", ctypes.c_uint32), ("cached", ctypes.c_uint32),
+                ("ms", ctypes.c_float)]
+
+
 class _InstrOpts(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int), ("skip", ctypes.POINTER(ctypes.c_char_p)),
                 ("nskip", ctypes.c_size_t)]
@@ -76,6 +95,14 @@ _SIG = {
                                            ctypes.c_float, ctypes.c_int, _P, _P]),
     "agile_irregular_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
                                               ctypes.c_int, _P, _P]),
+    "agile_batch_device_bytes": (ctypes.c_size_t, [ctypes.c_size_t]),
+    "agile_batch_upload": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, _P, ctypes.c_size_t, _P]),
+    "agile_batch_launch": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
+    "agile_batch_graph_create": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
+    "agile_graph_launch": (ctypes.c_int, [_P, _P]),
+    "agile_graph_destroy": (None, [_P]),
+    "agile_batch_autotune": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_size_t, _P, ctypes.c_size_t,
+                                            _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_char_p, _P, _P]),
     "agile_guard_instrument_ptx": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, _P, _P, _P, _P]),
     "agile_module_load": (ctypes.c_int, [ctypes.c_char_p, _P]),
     "agile_module_bind": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -286,6 +313,80 @@ def agile_irregular_launch(kind: str, dev: DevTable | None, d_idx, d_base, d_out
                                         _dptr(d_idx), _dptr(d_base), _dptr(d_out), n,
                                         POLICIES[policy], _dptr(d_log), _stream(stream)),
            "agile_irregular_launch")
+
+
+# ---------------------------------------------------------------- batched clients
+
+
+def make_work(op: str, dev: DevTable | None, out, in0, in1, n: int, s: float = 3.0,
+              policy: str = "poison", log=None, client: int = 0) -> Work:
+    return Work(WORK[op], POLICIES[policy], n, dev.address if dev is not None else None,
+                _dptr(log), _dptr(out), _dptr(in0), _dptr(in1), s, client)
+
+
+def agile_batch_device_bytes(max_items: int) -> int:
+    return lib().agile_batch_device_bytes(max_items)
+
+
+def agile_batch_upload(items, tile: int, d_buf, stream=None) -> None:
+    arr = (Work * len(items))(*items)
+    nbytes = d_buf.numel() * d_buf.element_size() if hasattr(d_buf, "numel") else \
+        agile_batch_device_bytes(len(items))
+    _check(lib().agile_batch_upload(arr, len(items), tile, _dptr(d_buf), nbytes, _stream(stream)),
+           "agile_batch_upload")
+
+
+def agile_batch_launch(d_buf, n_items: int, tile: int, span_checks: bool = True,
+                       blocks_per_sm: int = 2, stream=None) -> None:
+    cfg = BatchConfig(tile, int(span_checks), blocks_per_sm, 0)
+    _check(lib().agile_batch_launch(_dptr(d_buf), n_items, ctypes.byref(cfg), _stream(stream)),
+           "agile_batch_launch")
+
+
+class Graph:
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    def launch(self, stream=None) -> None:
+        _check(lib().agile_graph_launch(self._h, _stream(stream)), "agile_graph_launch")
+
+    def destroy(self) -> None:
+        if self._h.value:
+            lib().agile_graph_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            if _lib is not None:
+                self.destroy()
+        except Exception:
+            pass
+
+
+def agile_batch_graph_create(d_buf, n_items: int, tile: int, span_checks: bool = True,
+                             blocks_per_sm: int = 2) -> Graph:
+    cfg = BatchConfig(tile, int(span_checks), blocks_per_sm, 0)
+    out = ctypes.c_void_p()
+    _check(lib().agile_batch_graph_create(_dptr(d_buf), n_items, ctypes.byref(cfg), ctypes.byref(out)),
+           "agile_batch_graph_create")
+    return Graph(out.value)
+
+
+def agile_batch_autotune(variants, tiles, d_buf, reps: int = 3, cache_path: str | None = None,
+                         stream=None) -> dict:
+    """variants: list of equal-length work lists. Returns the winning configuration."""
+    n_items = len(variants[0])
+    flat = [w for v in variants for w in v]
+    arr = (Work * len(flat))(*flat)
+    tl = (ctypes.c_uint32 * len(tiles))(*tiles)
+    best = BatchTuning()
+    nbytes = d_buf.numel() * d_buf.element_size()
+    _check(lib().agile_batch_autotune(arr, len(variants), n_items, tl, len(tiles), _dptr(d_buf),
+                                      nbytes, reps, cache_path.encode() if cache_path else None,
+                                      _stream(stream), ctypes.byref(best)), "agile_batch_autotune")
+    c = best.config
+    return {"tile": c.tile, "span_checks": bool(c.span_checks), "blocks_per_sm": c.blocks_per_sm,
+            "variant": best.variant, "cached": bool(best.cached), "ms": best.ms}
 
 
 # ---------------------------------------------------------------- PTX guard pass

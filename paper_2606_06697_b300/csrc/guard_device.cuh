@@ -63,14 +63,18 @@ __host__ __device__ inline unsigned long long pack_info(uint32_t site, uint32_t 
 // The table as a kernel sees it: pointers into shared memory (staged copies) or global.
 struct TView {
     uint64_t lo, npages;
-    uint32_t lg, n;
+    uint64_t gmask;             // page size - 1
+    uint64_t last;              // last byte of the window (lo + npages*G - 1)
+    uint32_t lg, n, steps;
     const uint32_t *page;
     const uint64_t *base, *end;
     const uint32_t *kind, *id;
 };
 
 __device__ __forceinline__ TView view_of(const agile_dev_table_t &T) {
-    return TView{T.lo, T.npages, T.log2_page, T.n, T.page, T.base, T.end, T.kind, T.id};
+    const uint64_t G = 1ull << T.log2_page;
+    return TView{T.lo, T.npages, G - 1, T.lo + (T.npages << T.log2_page) - 1, T.log2_page, T.n,
+                 T.search_steps, T.page, T.base, T.end, T.kind, T.id};
 }
 
 __device__ __forceinline__ uint32_t deny_of_kind(uint32_t kind) {
@@ -78,17 +82,11 @@ __device__ __forceinline__ uint32_t deny_of_kind(uint32_t kind) {
          : kind == AGILE_PROTECTED ? AGILE_DENY_PROTECTED : AGILE_DENY_STRADDLE;
 }
 
-// Search ranges [lo_i, hi_i) for the last one starting at or below a, then walk the
-// ranges [a, a + w) touches in address order.
-__device__ __forceinline__ uint32_t search(const TView &V, uint32_t lo_i, uint32_t hi_i,
-                                          uint64_t a, uint64_t w, uint32_t *rid) {
-    uint32_t b = lo_i, len = hi_i - lo_i;
-    while (len > 0) {                       // b = first index in [lo_i, hi_i) with base > a
-        const uint32_t half = len >> 1;
-        const bool le = V.base[b + half] <= a;
-        b = le ? b + half + 1 : b;
-        len = le ? len - half - 1 : half;
-    }
+// After the search: b = first index with base > a among the slice that starts at lo_i.
+// Decide from range b-1 (allowed if it is a user range holding all of [a, a+w)), else
+// walk the ranges [a, a + w) touches in address order for the deny class.
+__device__ __forceinline__ uint32_t decide(const TView &V, uint32_t lo_i, uint32_t b, uint64_t a,
+                                          uint64_t w, uint32_t *rid) {
     uint32_t first = b;
     if (b > lo_i) {
         const uint32_t j = b - 1;
@@ -110,26 +108,49 @@ __device__ __forceinline__ uint32_t search(const TView &V, uint32_t lo_i, uint32
     return best == 0 ? AGILE_DENY_MMIO : best == 1 ? AGILE_DENY_PROTECTED : AGILE_DENY_STRADDLE;
 }
 
-// Verdict of [a, a + w), w >= 1 any size, fully inline.
+// Variable-length search over [lo_i, hi_i) (any slice; used outside the window).
+__device__ __forceinline__ uint32_t search(const TView &V, uint32_t lo_i, uint32_t hi_i,
+                                          uint64_t a, uint64_t w, uint32_t *rid) {
+    uint32_t b = lo_i, len = hi_i - lo_i;
+    while (len > 0) {                       // b = first index in [lo_i, hi_i) with base > a
+        const uint32_t half = len >> 1;
+        const bool le = V.base[b + half] <= a;
+        b = le ? b + half + 1 : b;
+        len = le ? len - half - 1 : half;
+    }
+    return decide(V, lo_i, b, a, w, rid);
+}
+
+// Verdict of [a, a + w), w >= 1 any size, fully inline. Inside the window the search
+// runs a fixed number of branchless steps (the table's search_steps covers every page's
+// slice), so lanes of a warp stay together; accesses wholly outside the window touch no
+// range.
 __device__ __forceinline__ uint32_t classify(const TView &V, uint64_t a, uint64_t w, uint32_t *rid) {
     if (w == 0 || a > ~0ull - w) { *rid = kNoRange; return AGILE_DENY_INVALID; }
     const uint64_t off = a - V.lo;
     const uint64_t p = off >> V.lg;
-    uint32_t lo_i = 0, hi_i = V.n;
     if (p < V.npages) {
         const uint32_t e = V.page[p];
         const uint32_t f = e & kIdxMask, ty = e >> 30;
-        const uint64_t G = 1ull << V.lg;
-        if ((off & (G - 1)) + w <= G) {
+        if ((off & V.gmask) + w <= V.gmask + 1) {
             if (ty == PG_USER) { *rid = kNoRange; return AGILE_ALLOW; }
             if (ty == PG_HOLE) { *rid = kNoRange; return AGILE_DENY_UNMAPPED; }
             if (ty == PG_DENY) { *rid = V.id[f]; return deny_of_kind(V.kind[f]); }
         }
         const uint32_t f2 = V.page[p + 1] & kIdxMask;
-        lo_i = f;
-        hi_i = f2 + 1 < V.n ? f2 + 1 : V.n;
+        const uint32_t hi_i = f2 + 1 < V.n ? f2 + 1 : V.n;
+        uint32_t b = f, len = hi_i > f ? hi_i - f : 0;
+        for (uint32_t it = 0; it < V.steps; ++it) {
+            const uint32_t half = len >> 1;
+            const uint32_t probe = b + half < V.n ? b + half : V.n - 1;
+            const bool le = len > 0 && V.base[probe] <= a;
+            b = le ? b + half + 1 : b;
+            len = le ? len - half - 1 : half;
+        }
+        return decide(V, f, b, a, w, rid);
     }
-    return search(V, lo_i, hi_i, a, w, rid);
+    if (a + w <= V.lo || a > V.last) { *rid = kNoRange; return AGILE_DENY_UNMAPPED; }
+    return search(V, 0, V.n, a, w, rid);
 }
 
 // Out-of-line form for paths where the common case is decided elsewhere.

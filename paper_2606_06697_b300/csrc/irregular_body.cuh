@@ -1,0 +1,110 @@
+// Guarded irregular bodies shared by the standalone kernels and the batched persistent
+// kernel: gather out[i] = T[idx[i]], scatter T[idx[i]] = (float)(idx[i] & 0xFFFFFF),
+// histogram bins[idx[i]] += 1, with int64 element offsets an untrusted kernel could aim
+// anywhere.
+//
+// Each lane takes four consecutive elements: the index array is read as two 16-byte
+// loads (sites 0 and 1) and the output stored as one 16-byte store (site 3), contiguous
+// across the warp, so one warp-uniform span check decides them; the four element
+// accesses (site 2) go to data-dependent addresses and are checked per lane -- a page-map
+// lookup, and a binary search only on mixed pages. The n mod 4 tail elements use an
+// 8-byte index load, the element access and a 4-byte store. Each thread keeps its
+// smallest violation in a LaneLog.
+#pragma once
+
+#include "guard_device.cuh"
+
+namespace agile {
+
+__device__ __forceinline__ bool lane_check(const TView &V, uint64_t a, uint32_t w, uint32_t site,
+                                           LaneLog &ll) {
+    uint32_t rid;
+    const uint32_t v = classify(V, a, w, &rid);
+    if (v == AGILE_ALLOW) return true;
+    ll.note(a, pack_info(site, v, w, rid), a);
+    return false;
+}
+
+template <int KIND, int POLICY>
+__device__ __forceinline__ float element(float *addr, bool ok, int64_t e, const agile_dev_table_t &T) {
+    constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
+    if constexpr (KIND == AGILE_IRR_GATHER) {
+        return __ldg((ok || kAlways) ? addr : reinterpret_cast<const float *>(T.zero_page));
+    } else if constexpr (KIND == AGILE_IRR_SCATTER) {
+        const float f = (float)((uint64_t)e & 0xFFFFFFu);
+        if (ok || kAlways) *addr = f;
+        else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = f;
+        return 0.f;
+    } else {
+        if (ok || kAlways) atomicAdd(reinterpret_cast<unsigned int *>(addr), 1u);
+        else if constexpr (POLICY == AGILE_POLICY_SINK)
+            atomicAdd(reinterpret_cast<unsigned int *>(T.sink_page), 1u);
+        return 0.f;
+    }
+}
+
+// Units u0 .. u0+31 (one per lane, clipped to n4). Warp-collective only in its uniform
+// span checks; `spans` off means every index/output access is checked per lane.
+template <int KIND, bool GUARD, int POLICY>
+__device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_table_t &T,
+                                                const int64_t *idx, float *base, float *out,
+                                                size_t u0, size_t n4, LaneLog &ll, bool spans) {
+    constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
+    constexpr bool kGather = KIND == AGILE_IRR_GATHER;
+    const longlong2 *idx2 = reinterpret_cast<const longlong2 *>(idx);
+    const longlong2 *zero2 = reinterpret_cast<const longlong2 *>(T.zero_page);
+    float4 *out4 = reinterpret_cast<float4 *>(out);
+    const size_t u = u0 + (threadIdx.x & 31);
+    const bool act = u < n4;
+    bool ok0 = true, ok1 = true, oko = true;
+    if constexpr (GUARD) {
+        const bool full = spans && u0 + 32 <= n4;
+        const bool fast_i = full && span_allowed(V, (uint64_t)(idx2 + 2 * u0), 1024);
+        if (!fast_i && act) {
+            ok0 = lane_check(V, (uint64_t)(idx2 + 2 * u), 16, 0, ll);
+            ok1 = lane_check(V, (uint64_t)(idx2 + 2 * u + 1), 16, 1, ll);
+        }
+        if constexpr (kGather) {
+            const bool fast_o = full && span_allowed(V, (uint64_t)(out4 + u0), 512);
+            if (!fast_o && act) oko = lane_check(V, (uint64_t)(out4 + u), 16, 3, ll);
+        }
+    }
+    if (!act) return;
+    const longlong2 p0 = __ldg((ok0 || kAlways) ? idx2 + 2 * u : zero2);
+    const longlong2 p1 = __ldg((ok1 || kAlways) ? idx2 + 2 * u + 1 : zero2);
+    const int64_t e[4] = {p0.x, p0.y, p1.x, p1.y};
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float *addr = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e[k]);
+        const bool ok = !GUARD || lane_check(V, (uint64_t)addr, 4, 2, ll);
+        v[k] = element<KIND, POLICY>(addr, ok, e[k], T);
+    }
+    if constexpr (kGather) {
+        const float4 o = make_float4(v[0], v[1], v[2], v[3]);
+        if (oko || kAlways) __stcs(out4 + u, o);
+        else if constexpr (POLICY == AGILE_POLICY_SINK) __stcs(reinterpret_cast<float4 *>(T.sink_page), o);
+    }
+}
+
+// The n mod 4 tail elements, lanes 0..2 of one warp.
+template <int KIND, bool GUARD, int POLICY>
+__device__ __forceinline__ void irregular_tail(const TView &V, const agile_dev_table_t &T,
+                                               const int64_t *idx, float *base, float *out,
+                                               size_t n, LaneLog &ll) {
+    constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
+    const size_t i = (n >> 2) * 4 + (threadIdx.x & 31);
+    if (i >= n) return;
+    const bool oki = !GUARD || lane_check(V, (uint64_t)(idx + i), 8, 0, ll);
+    const int64_t e = *((oki || kAlways) ? idx + i : reinterpret_cast<const int64_t *>(T.zero_page));
+    float *addr = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e);
+    const bool ok = !GUARD || lane_check(V, (uint64_t)addr, 4, 2, ll);
+    const float v = element<KIND, POLICY>(addr, ok, e, T);
+    if constexpr (KIND == AGILE_IRR_GATHER) {
+        const bool oko = !GUARD || lane_check(V, (uint64_t)(out + i), 4, 3, ll);
+        if (oko || kAlways) out[i] = v;
+        else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = v;
+    }
+}
+
+}  // namespace agile

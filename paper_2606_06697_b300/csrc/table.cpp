@@ -47,6 +47,18 @@ void build_pages(agile_guard_table &t) {
         t.page[p] = (type << 30) | j;
     }
     t.page[t.npages] = (PG_HOLE << 30) | t.n;
+    // A search inside page p runs over base[f_p, min(f_{p+1} + 1, n)); a slice of L ranges
+    // needs floor(log2 L) + 1 halving steps.
+    uint32_t steps = 0;
+    for (uint64_t p = 0; p < t.npages; ++p) {
+        const uint32_t f = t.page[p] & kIdxMask, f2 = t.page[p + 1] & kIdxMask;
+        const uint32_t hi = f2 + 1 < t.n ? f2 + 1 : t.n;
+        const uint32_t len = hi > f ? hi - f : 0;
+        uint32_t k = 0;
+        while ((len >> k) != 0) ++k;
+        if (k > steps) steps = k;
+    }
+    t.search_steps = steps;
 }
 
 }  // namespace
@@ -172,6 +184,7 @@ int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, 
     h.zero_page = d + kZeroOff;
     h.sink_page = d + kSinkOff;
     h.bytes = t->total;
+    h.search_steps = t->search_steps;
     static_assert(sizeof(agile_dev_table_t) <= kHeaderBytes, "header fits");
     std::memcpy(t->staging.data(), &h, sizeof h);
     std::memset(t->staging.data() + kZeroOff, 0, 128);
