@@ -41,6 +41,7 @@ WORKLOAD = ("guarded streaming copy/scale/triad, 3 fp32 arrays of 2^28 elements 
             "in an arena under a 1096-range guard table (1024 user, 64 protected, 8 MMIO), "
             "2 MiB pages, poison policy")
 KERNEL_SOURCES = ["paper_2606_06697_b300/csrc/stream.cu",
+                  "paper_2606_06697_b300/csrc/stream_body.cuh",
                   "paper_2606_06697_b300/csrc/guard_device.cuh"]
 
 
