@@ -301,6 +301,22 @@ AGILE_API int agile_batch_graph_create(void *d_buf, size_t n_items, const agile_
 AGILE_API int agile_graph_launch(agile_graph_t *g, void *stream);
 AGILE_API void agile_graph_destroy(agile_graph_t *g);
 
+/* Maximum work items of agile_batch_launch_static. */
+#define AGILE_BATCH_STATIC_MAX_ITEMS 2048
+
+/* agile_batch_upload + agile_batch_launch without any device allocation: the batch's
+ * scratch (work list, tile prefix sums, tile-claim counter) lives in a fixed device
+ * array inside the library (about 147 KB, held by every GPU that loads the library).
+ * The paper has no counterpart; it is for callers that cannot allocate device memory --
+ * a worker whose budget is fully handed out, code that must avoid the implicit
+ * synchronization of cudaMalloc/cudaFree, a plugin given no allocator. The caller still
+ * provides every input and output. TOO_LARGE above AGILE_BATCH_STATIC_MAX_ITEMS items;
+ * other errors as agile_batch_upload. The first call on a device looks up the array's
+ * device address, so make it before any stream capture. All calls share the array:
+ * calls that overlap on the GPU race. */
+AGILE_API int agile_batch_launch_static(const agile_work_t *h_items, size_t n, uint32_t tile,
+                                        const agile_batch_config_t *cfg, void *stream);
+
 /* Pick the fastest launch for a batch: every variant (n_variants work lists of n_items
  * each, back to back in h_variants -- e.g. the same work with tables of different page
  * sizes) x every candidate tile x span checks on/off x 1 or 2 blocks per SM, timed with

@@ -101,6 +101,7 @@ _SIG = {
     "agile_batch_graph_create": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
     "agile_graph_launch": (ctypes.c_int, [_P, _P]),
     "agile_graph_destroy": (None, [_P]),
+    "agile_batch_launch_static": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, _P, _P]),
     "agile_batch_autotune": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_size_t, _P, ctypes.c_size_t,
                                             _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_char_p, _P, _P]),
     "agile_guard_instrument_ptx": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, _P, _P, _P, _P]),
@@ -341,6 +342,21 @@ def agile_batch_launch(d_buf, n_items: int, tile: int, span_checks: bool = True,
     cfg = BatchConfig(tile, int(span_checks), blocks_per_sm, 0)
     _check(lib().agile_batch_launch(_dptr(d_buf), n_items, ctypes.byref(cfg), _stream(stream)),
            "agile_batch_launch")
+
+
+BATCH_STATIC_MAX_ITEMS = 2048
+
+
+def agile_batch_launch_static(items, tile: int, span_checks: bool = True, blocks_per_sm: int = 2,
+                              stream=None) -> None:
+    """agile_batch_launch without a device buffer from the caller: for callers that cannot
+    allocate device memory (their budget is spoken for, they must avoid the implicit
+    synchronization of an allocation, or their host gives them no allocator). The
+    library's own fixed scratch array holds the work list; concurrent calls race on it."""
+    arr = (Work * len(items))(*items)
+    cfg = BatchConfig(tile, int(span_checks), blocks_per_sm, 0)
+    _check(lib().agile_batch_launch_static(arr, len(items), tile, ctypes.byref(cfg), _stream(stream)),
+           "agile_batch_launch_static")
 
 
 class Graph:

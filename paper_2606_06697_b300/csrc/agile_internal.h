@@ -27,6 +27,10 @@ namespace agile {
 // agile_validate_args and by the serving loop's admission checks.
 uint32_t classify_host(const agile_guard_table &t, uint64_t a, uint64_t w, uint32_t *rid);
 
+// Validation of one batch work item (kind, policy, size, alignment), as the batch upload
+// applies it.
+int batch_check_item(const agile_work_t &w);
+
 // Remember the last CUDA error text for agile_strerror-style diagnostics.
 void set_cuda_error(int err, const char *where);
 int sm_count();

@@ -185,6 +185,10 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
 
 }  // namespace
 
+namespace agile {
+int batch_check_item(const agile_work_t &w) { return check_item(w); }
+}  // namespace agile
+
 extern "C" {
 
 size_t agile_batch_device_bytes(size_t max_items) {
