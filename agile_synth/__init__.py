@@ -459,3 +459,104 @@ def client_indices(spec: dict, n: int, seed: int = SEED_BASE + 4, frac_bad: floa
     if nbad and bad_target is not None:
         idx[np.unique(st.below(n, nbad))] = bad_target
     return idx
+
+
+# ---------------------------------------------------------------- serving
+
+SERVE_SLOTS = 4
+
+
+def serve_specs(n_clients: int = 64, seed: int = SEED_BASE + 5, median: int = 8 * MiB,
+                lo: int = 64 * KiB, hi: int = 1 * GiB, **kw):
+    """64 clients in the batched mix, one buffer size each (lognormal, median 8 MiB,
+    clamped to [64 KiB, 1 GiB])."""
+    return client_specs(n_clients, seed=seed, median=median, lo=lo, hi=hi, table_lo=8,
+                        table_hi=512, **kw)
+
+
+def serve_layout(spec: dict, seed: int = SEED_BASE + 5, slots: int = SERVE_SLOTS):
+    """A served client's arena: its input buffers, `slots` output buffers (requests of a
+    client take turns on them), decoys, and four decoy allocations that are later freed
+    (kept out of the table). Returns (ranges_relative, freed_mask, arena_bytes,
+    {buffer: offset}, {buffer: bytes}, n)."""
+    st = Stream(seed, 300 + spec["client"])
+    B = spec["bytes"]
+    if spec["op"] == "copy":
+        n = B // 4
+        bufs = {"b": B} | {f"out{k}": B for k in range(slots)}
+    elif spec["op"] == "gather":
+        n = max(B // 16, 1)
+        bufs = {"t": B, "idx": 8 * n} | {f"out{k}": 4 * n for k in range(slots)}
+    else:
+        n = max(B // 8, 1)
+        bufs = {"idx": 8 * n} | {f"out{k}": 4 * HIST_BINS for k in range(slots)}
+    names = list(bufs)
+    nd = max(spec["ranges"] - len(names), 8)
+    dsize = st.log_uniform(4 * KiB, 64 * KiB, nd)
+    u = st.uniform(nd)
+    dkind = np.where(u < 0.8, KIND_USER, np.where(u < 0.95, KIND_PROTECTED, KIND_MMIO))
+    dkind[:2] = KIND_PROTECTED                       # every client has protected decoys
+    sizes = np.concatenate([[bufs[k] for k in names], dsize]).astype(np.int64)
+    kinds = np.concatenate([[KIND_USER] * len(names), dkind])
+    freed_ids = set(range(0x1000 + len(names) + 2, 0x1000 + len(names) + 6))
+    span = _round_up(int(_round_up(sizes, 256).sum()) + (len(sizes) + 1) * 8 * KiB, 2 * MiB)
+    r = layout(st, sizes, kinds, span, 0, min_gap=4 * KiB, align=256)
+    freed = np.isin(r.ident, list(freed_ids)) & (r.kind == KIND_USER)
+    return r, freed, span, {k: find(r, 0x1000 + i) for i, k in enumerate(names)}, bufs, n
+
+
+def poisson_arrivals(stream: Stream, rate: float, n: int) -> np.ndarray:
+    """Arrival times (ns) of a Poisson process of `rate` per second."""
+    gaps = -np.log(1.0 - stream.uniform(n)) / rate
+    return (np.cumsum(gaps) * 1e9).astype(np.int64)
+
+
+def serve_requests(layouts, rate: float, n: int, seed: int = SEED_BASE + 5,
+                   frac_bad: float = 0.005, start_ns: int = 0):
+    """Requests from the clients: Poisson arrivals at `rate`, a uniformly chosen client,
+    its next output slot in turn, 1-16 pointer arguments (the buffers the kernel touches,
+    then sub-ranges of the client's buffers), and for int(n * frac_bad) of them one
+    argument replaced by a bad pointer -- into a protected decoy, into a freed allocation,
+    or straddling the end of a buffer, in equal thirds. Offsets are arena-relative.
+
+    Returns a list of dicts: client, slot, arrival_ns, args [(off, bytes)], bad (None or
+    'protected' / 'freed' / 'straddle'), bad_arg."""
+    st = Stream(seed, 400 + int(rate))
+    arr = poisson_arrivals(st, rate, n) + start_ns
+    who = st.below(len(layouts), n)
+    nargs = 1 + st.below(16, n)
+    nbad = int(n * frac_bad)
+    bad_pos = set(np.unique(st.below(n, nbad)).tolist()) if nbad else set()
+    turn = [0] * len(layouts)
+    out = []
+    for i in range(n):
+        c = int(who[i])
+        r, freed, span, off, sizes, _ = layouts[c]
+        slot = turn[c] % SERVE_SLOTS
+        turn[c] += 1
+        ins = [k for k in off if not k.startswith("out")]
+        touched = ins + [f"out{slot}"]
+        args = [(off[k], sizes[k]) for k in touched]
+        while len(args) < nargs[i]:
+            k = ins[int(st.below(len(ins), 1)[0])]
+            lo = int(st.below(sizes[k], 1)[0])
+            ln = 1 + int(st.below(sizes[k] - lo, 1)[0])
+            args.append((off[k] + lo, ln))
+        args = args[:max(int(nargs[i]), len(touched))][:16]
+        req = {"client": c, "slot": slot, "arrival_ns": int(arr[i]), "args": args, "bad": None,
+               "bad_arg": None}
+        if i in bad_pos:
+            kind = ("protected", "freed", "straddle")[i % 3]
+            j = int(st.below(len(args), 1)[0])
+            if kind == "protected":
+                p = np.flatnonzero(r.kind == KIND_PROTECTED)[0]
+                args[j] = (int(r.base[p]), 16)
+            elif kind == "freed":
+                p = np.flatnonzero(freed)[0]
+                args[j] = (int(r.base[p]), 64)
+            else:
+                k = touched[0]
+                args[j] = (off[k] + sizes[k] - 8, 16)
+            req.update(bad=kind, bad_arg=j)
+        out.append(req)
+    return out

@@ -330,6 +330,79 @@ AGILE_API int agile_batch_autotune(const agile_work_t *h_variants, size_t n_vari
                                    void *d_buf, size_t bytes, int reps, const char *cache_path,
                                    void *stream, agile_batch_tuning_t *best);
 
+/* ---------------------------------------------------------------- serving worker */
+
+#define AGILE_MAX_ARGS 16
+
+/* One client request: validate its pointer arguments, then run its guarded kernel. */
+typedef struct {
+    uint64_t tag;                       /* caller's id, echoed in the completion            */
+    uint32_t client;                    /* client index given to agile_worker_create         */
+    uint32_t nargs;                     /* pointer arguments to validate (<= AGILE_MAX_ARGS) */
+    uint64_t arg_ptr[AGILE_MAX_ARGS];
+    uint64_t arg_bytes[AGILE_MAX_ARGS];
+    agile_work_t work;                  /* its kernel; NULL table/log take the client's      */
+    uint64_t mem_bytes;                 /* device memory it holds while admitted             */
+    uint64_t excl;                      /* nonzero: requests with equal keys never overlap    */
+    uint64_t arrival_ns;                /* arrival time on the worker clock (ns from start)  */
+} agile_request_t;
+
+/* What happened to a request. */
+typedef struct {
+    uint64_t tag;
+    int32_t status;                     /* AGILE_OK; AGILE_VIOLATION: rejected at validation;
+                                           AGILE_ERR_TOO_LARGE: can never fit the budget     */
+    uint32_t bad_arg;                   /* first denied argument (rejections)                */
+    uint32_t verdict;                   /* its verdict                                       */
+    uint32_t launch;                    /* sequence number of the launch that ran it         */
+    uint64_t arrival_ns, admit_ns, done_ns;
+} agile_completion_t;
+
+typedef struct {
+    uint64_t mem_budget;                /* cap on the sum of admitted requests' mem_bytes    */
+    uint32_t max_batch;                 /* requests per launch                               */
+    uint32_t max_inflight;              /* launches in flight, one stream each              */
+    uint32_t tile;                      /* batch tile (multiple of 512)                      */
+    uint32_t continuous;                /* 1: continuous batching; 0: one request at a time  */
+} agile_worker_config_t;
+
+typedef struct agile_worker agile_worker_t;
+
+/* Device bytes of the worker's batch buffers (max_inflight of them). */
+AGILE_API size_t agile_worker_device_bytes(const agile_worker_config_t *cfg);
+
+/* A worker serving n_clients clients (Sec. IV-B: a trusted worker owns the context and
+ * executes the clients' requests; Sec. IV-C / V-C: every pointer argument is validated
+ * against the client's live allocations before any launch). h_tables[i] (host, for
+ * validation) and d_tables[i] (uploaded, for the guard) are client i's table; d_logs[i]
+ * its log. d_buf (256-byte aligned, agile_worker_device_bytes) holds the launches' work
+ * lists. The worker thread starts with agile_worker_start; its clock starts there.
+ * Tables, logs and d_buf must outlive the worker. */
+AGILE_API int agile_worker_create(const agile_worker_config_t *cfg,
+                                  const agile_guard_table_t *const *h_tables,
+                                  const agile_dev_table_t *const *d_tables, void *const *d_logs,
+                                  size_t n_clients, void *d_buf, size_t bytes,
+                                  agile_worker_t **out);
+
+/* Queue requests (thread-safe, any time). Each is considered once the worker clock
+ * passes its arrival time: validated (a denied argument completes it at once with
+ * AGILE_VIOLATION), then admitted in arrival order when the memory budget, a launch slot
+ * and its exclusive key allow; admitted requests are packed into the next persistent
+ * launch while earlier launches still run (continuous batching). */
+AGILE_API int agile_worker_submit(agile_worker_t *w, const agile_request_t *reqs, size_t n);
+AGILE_API int agile_worker_start(agile_worker_t *w);
+
+/* Take up to cap completions; waits up to wait_ms for at least one. */
+AGILE_API int agile_worker_poll(agile_worker_t *w, agile_completion_t *out, size_t cap,
+                                size_t *got, uint32_t wait_ms);
+
+/* Current worker clock (ns since start) and admitted bytes (for tests of the budget). */
+AGILE_API int agile_worker_clock(agile_worker_t *w, uint64_t *now_ns, uint64_t *admitted_bytes,
+                                 uint64_t *peak_admitted_bytes);
+
+/* Stop after every queued request has completed, then free the worker. */
+AGILE_API void agile_worker_destroy(agile_worker_t *w);
+
 /* ---------------------------------------------------------------- PTX guard pass */
 
 typedef struct {

@@ -7,6 +7,7 @@ supplies device memory and streams. The names match the C entry points declared 
 from __future__ import annotations
 
 from .abi import (  # noqa: F401
+    Completion, Request, Worker, WorkerConfig, agile_worker_device_bytes,
     Graph, Work, agile_batch_autotune, agile_batch_launch_static, BATCH_STATIC_MAX_ITEMS, agile_batch_device_bytes, agile_batch_graph_create,
     agile_batch_launch, agile_batch_upload, make_work, WORK,
     AgileError, DevTable, Module, Table, ViolationRecord, agile_free, agile_guard_check_batch,

@@ -70,6 +70,28 @@ class BatchTuning(ctypes.Structure):
                 ("ms", ctypes.c_float)]
 
 
+class Request(ctypes.Structure):
+    """agile_request_t."""
+    _fields_ = [("tag", ctypes.c_uint64), ("client", ctypes.c_uint32), ("nargs", ctypes.c_uint32),
+                ("arg_ptr", ctypes.c_uint64 * 16), ("arg_bytes", ctypes.c_uint64 * 16),
+                ("work", Work), ("mem_bytes", ctypes.c_uint64), ("excl", ctypes.c_uint64),
+                ("arrival_ns", ctypes.c_uint64)]
+
+
+class Completion(ctypes.Structure):
+    """agile_completion_t."""
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("bad_arg", ctypes.c_uint32),
+                ("verdict", ctypes.c_uint32), ("launch", ctypes.c_uint32),
+                ("arrival_ns", ctypes.c_uint64), ("admit_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64)]
+
+
+class WorkerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("tile", ctypes.c_uint32),
+                ("continuous", ctypes.c_uint32)]
+
+
 class _InstrOpts(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int), ("skip", ctypes.POINTER(ctypes.c_char_p)),
                 ("nskip", ctypes.c_size_t)]
@@ -104,6 +126,13 @@ _SIG = {
     "agile_batch_launch_static": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, _P, _P]),
     "agile_batch_autotune": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_size_t, _P, ctypes.c_size_t,
                                             _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_char_p, _P, _P]),
+    "agile_worker_device_bytes": (ctypes.c_size_t, [_P]),
+    "agile_worker_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_size_t, _P, ctypes.c_size_t, _P]),
+    "agile_worker_submit": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "agile_worker_start": (ctypes.c_int, [_P]),
+    "agile_worker_poll": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, ctypes.c_uint32]),
+    "agile_worker_clock": (ctypes.c_int, [_P, _P, _P, _P]),
+    "agile_worker_destroy": (None, [_P]),
     "agile_guard_instrument_ptx": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, _P, _P, _P, _P]),
     "agile_module_load": (ctypes.c_int, [ctypes.c_char_p, _P]),
     "agile_module_bind": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -403,6 +432,61 @@ def agile_batch_autotune(variants, tiles, d_buf, reps: int = 3, cache_path: str 
     c = best.config
     return {"tile": c.tile, "span_checks": bool(c.span_checks), "blocks_per_sm": c.blocks_per_sm,
             "variant": best.variant, "cached": bool(best.cached), "ms": best.ms}
+
+
+# ---------------------------------------------------------------- serving worker
+
+
+class Worker:
+    """A native serving worker (agile_worker_*). Keeps references to what it uses."""
+
+    def __init__(self, cfg: WorkerConfig, tables, devs, logs, d_buf):
+        n = len(tables)
+        self._keep = (tables, devs, logs, d_buf)
+        ht = (ctypes.c_void_p * n)(*[t.handle.value for t in tables])
+        self._views = [d.view for d in devs]
+        dt = (ctypes.c_void_p * n)(*[ctypes.addressof(v) for v in self._views])
+        dl = (ctypes.c_void_p * n)(*[_dptr(x) for x in logs])
+        out = ctypes.c_void_p()
+        nbytes = d_buf.numel() * d_buf.element_size()
+        _check(lib().agile_worker_create(ctypes.byref(cfg), ht, dt, dl, n, _dptr(d_buf), nbytes,
+                                         ctypes.byref(out)), "agile_worker_create")
+        self._h = out
+
+    def submit(self, reqs) -> None:
+        arr = (Request * len(reqs))(*reqs)
+        _check(lib().agile_worker_submit(self._h, arr, len(reqs)), "agile_worker_submit")
+
+    def start(self) -> None:
+        _check(lib().agile_worker_start(self._h), "agile_worker_start")
+
+    def poll(self, cap: int = 4096, wait_ms: int = 50):
+        arr = (Completion * cap)()
+        got = ctypes.c_size_t()
+        _check(lib().agile_worker_poll(self._h, arr, cap, ctypes.byref(got), wait_ms), "agile_worker_poll")
+        return [arr[i] for i in range(got.value)]
+
+    def clock(self):
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().agile_worker_clock(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "agile_worker_clock")
+        return a.value, b.value, c.value
+
+    def destroy(self) -> None:
+        if self._h and self._h.value:
+            lib().agile_worker_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            if _lib is not None:
+                self.destroy()
+        except Exception:
+            pass
+
+
+def agile_worker_device_bytes(cfg: WorkerConfig) -> int:
+    return lib().agile_worker_device_bytes(ctypes.byref(cfg))
 
 
 # ---------------------------------------------------------------- PTX guard pass

@@ -22,11 +22,40 @@ using agile::TView;
 
 constexpr int kThreads = 512;
 
+// Branch-light form of the rule for random access streams: every lane reads its page
+// entry and runs the same fixed number of binary-search steps over its page's range
+// slice, and the allow decision is made with selects, so a warp stays converged on the
+// common path. An access allowed by its page entry (all-user page) or by the range the
+// search lands on is decided here; everything else -- denials, accesses across the
+// window edge, illegal widths -- takes the full classification out of line.
+__device__ __forceinline__ bool allow_uniform(const TView &V, uint64_t a, uint32_t w) {
+    const uint64_t off = a - V.lo;
+    const bool inwin = (off >> V.lg) < V.npages;
+    const uint32_t p = inwin ? (uint32_t)(off >> V.lg) : 0u;
+    const uint32_t e = V.page[p], e2 = V.page[p + 1];
+    const uint32_t f = e & agile::kIdxMask, f2 = e2 & agile::kIdxMask;
+    const bool fast = inwin && (e >> 30) == agile::PG_USER && (off & V.gmask) + w <= V.gmask + 1;
+    const uint32_t hi = f2 + 1 < V.n ? f2 + 1 : V.n;
+    uint32_t b = f, len = (inwin && hi > f) ? hi - f : 0u;
+    for (uint32_t it = 0; it < V.steps; ++it) {
+        const uint32_t half = len >> 1;
+        const uint32_t probe = b + half < V.n ? b + half : (V.n ? V.n - 1 : 0u);
+        const bool le = len > 0 && V.base[probe] <= a;
+        b = le ? b + half + 1 : b;
+        len = le ? len - half - 1 : half;
+    }
+    const uint32_t j = b > f ? b - 1 : 0u;          // index 0 exists (npages > 0 implies n > 0)
+    const bool hit = b > f && V.kind[j] == AGILE_USER && V.end[j] >= a + w;   // base[j] <= a
+    return fast || hit;
+}
+
 __device__ __forceinline__ uint32_t check_one(const TView &V, uint64_t a, uint32_t w, size_t i,
                                               LaneLog &ll) {
+    const bool legal = w != 0 && w <= 16 && (w & (w - 1)) == 0 && a <= ~0ull - w;
+    if (legal && V.npages > 0 && allow_uniform(V, a, w)) return AGILE_ALLOW;
     uint32_t rid = agile::kNoRange;
-    const bool legal = w != 0 && w <= 16 && (w & (w - 1)) == 0;
-    const uint32_t v = legal ? agile::classify(V, a, w, &rid) : (uint32_t)AGILE_DENY_INVALID;
+    const uint32_t v = (w != 0 && w <= 16 && (w & (w - 1)) == 0)
+                           ? agile::classify_slow(V, a, w, &rid) : (uint32_t)AGILE_DENY_INVALID;
     if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
     return v;
 }
@@ -48,17 +77,19 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     for (size_t g = tid; g < ngroups; g += nthreads) {
         if constexpr (VEC == 8) {
             const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
-            uint4 q[4];
+            uint64_t av[8];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = __ldcs(pa + k);
+            for (int k = 0; k < 4; ++k) {              // registers only: no indexed arrays
+                const uint4 q = __ldcs(pa + k);
+                av[2 * k] = (uint64_t)q.y << 32 | q.x;
+                av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
+            }
             const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
             uint64_t out = 0;
-#pragma unroll 2
+#pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const uint4 &h = q[k >> 1];
-                const uint64_t a = (k & 1) ? ((uint64_t)h.w << 32 | h.z) : ((uint64_t)h.y << 32 | h.x);
                 const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
-                out |= (uint64_t)check_one(V, a, w, g * 8 + k, ll) << (8 * k);
+                out |= (uint64_t)check_one(V, av[k], w, g * 8 + k, ll) << (8 * k);
             }
             __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), (unsigned long long)out);
         } else {

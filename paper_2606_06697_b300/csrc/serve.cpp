@@ -1,0 +1,345 @@
+// Serving worker: a trusted worker thread that takes client requests as they arrive,
+// validates every pointer argument against the client's live allocations before any
+// launch (Sec. IV-C: the worker mediates every operation; Sec. V-C: pointers are resolved
+// against the allocation table and rejected if not inside one live allocation), admits
+// validated requests in arrival order under a device-memory budget, and packs the
+// admitted requests into persistent batched launches -- each kernel guarded by its
+// client's table (Sec. V-E) -- while earlier launches are still running (continuous
+// batching). Requests that carry the same exclusive key never run at the same time, so
+// a request's outputs are the same alone and in the mix.
+//
+// Per launch slot: one stream, one event, one pinned host staging image and one region
+// of the caller's device buffer holding the work list. The worker clock is
+// steady_clock nanoseconds since agile_worker_start.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <queue>
+#include <thread>
+#include <unordered_set>
+#include <vector>
+
+#include "agile_internal.h"
+
+namespace {
+
+size_t slot_bytes(uint32_t max_batch) { return agile_batch_device_bytes(max_batch); }
+
+struct Slot {
+    bool busy = false;
+    std::vector<uint32_t> reqs;
+    uint64_t mem = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    unsigned char *staging = nullptr;   // pinned
+    unsigned char *dev = nullptr;
+};
+
+}  // namespace
+
+struct agile_worker {
+    agile_worker_config_t cfg{};
+    std::vector<const agile_guard_table *> htab;
+    std::vector<const agile_dev_table_t *> dtab;
+    std::vector<void *> dlog;
+    std::vector<Slot> slots;
+    int device = 0;
+
+    std::mutex mu_in;
+    std::vector<agile_request_t> incoming;
+    std::mutex mu_out;
+    std::condition_variable cv_out;
+    std::deque<agile_completion_t> ready;
+
+    std::thread th;
+    std::atomic<bool> stop{false};
+    std::atomic<bool> started{false};
+    std::chrono::steady_clock::time_point t0;
+    std::atomic<uint64_t> admitted_pub{0}, peak_pub{0};
+    std::atomic<uint64_t> submitted{0}, completed{0};
+
+    // worker-thread state
+    std::vector<agile_request_t> reqs;
+    std::vector<agile_completion_t> comp;
+    std::priority_queue<std::pair<uint64_t, uint32_t>, std::vector<std::pair<uint64_t, uint32_t>>,
+                        std::greater<std::pair<uint64_t, uint32_t>>> arrivals;
+    std::deque<uint32_t> waiting;
+    std::unordered_set<uint64_t> busy_keys;
+    uint64_t admitted = 0;
+    uint32_t launches = 0;
+
+    uint64_t now() const {
+        return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                   std::chrono::steady_clock::now() - t0).count();
+    }
+
+    void finish(uint32_t id, int32_t status, uint32_t bad_arg, uint32_t verdict, uint64_t t) {
+        agile_completion_t &c = comp[id];
+        c.tag = reqs[id].tag;
+        c.status = status;
+        c.bad_arg = bad_arg;
+        c.verdict = verdict;
+        c.arrival_ns = reqs[id].arrival_ns;
+        c.done_ns = t;
+        {
+            std::lock_guard<std::mutex> g(mu_out);
+            ready.push_back(c);
+        }
+        completed.fetch_add(1);
+        cv_out.notify_all();
+    }
+
+    void take_incoming() {
+        std::vector<agile_request_t> in;
+        {
+            std::lock_guard<std::mutex> g(mu_in);
+            in.swap(incoming);
+        }
+        for (const agile_request_t &r : in) {
+            const uint32_t id = (uint32_t)reqs.size();
+            reqs.push_back(r);
+            comp.push_back(agile_completion_t{});
+            arrivals.push({r.arrival_ns, id});
+        }
+    }
+
+    // Validation at arrival: every pointer argument inside one live user allocation of
+    // the request's client; the kernel's work item well formed; the request able to fit
+    // the budget at all.
+    void arrive(uint32_t id, uint64_t t) {
+        agile_request_t &r = reqs[id];
+        if (r.client >= htab.size() || r.nargs > AGILE_MAX_ARGS) {
+            finish(id, AGILE_ERR_INVALID_ARG, 0, 0, t);
+            return;
+        }
+        for (uint32_t k = 0; k < r.nargs; ++k) {
+            uint32_t rid;
+            const uint32_t v = agile::classify_host(*htab[r.client], r.arg_ptr[k], r.arg_bytes[k], &rid);
+            if (v != AGILE_ALLOW) {
+                finish(id, AGILE_VIOLATION, k, v, t);
+                return;
+            }
+        }
+        if (r.work.table == nullptr)                 // the table buffer starts 256 B before its page map
+            r.work.table = reinterpret_cast<const unsigned char *>(dtab[r.client]->page) - 256;
+        if (r.work.log == nullptr) r.work.log = dlog[r.client];
+        const int rc = agile::batch_check_item(r.work);
+        if (rc != AGILE_OK) { finish(id, rc, 0, 0, t); return; }
+        if (r.mem_bytes > cfg.mem_budget) { finish(id, AGILE_ERR_TOO_LARGE, 0, 0, t); return; }
+        waiting.push_back(id);
+    }
+
+    bool any_busy() const {
+        for (const Slot &s : slots) if (s.busy) return true;
+        return false;
+    }
+
+    void reap(uint64_t t) {
+        for (Slot &s : slots) {
+            if (!s.busy || cudaEventQuery(s.done) != cudaSuccess) continue;
+            for (uint32_t id : s.reqs) {
+                if (reqs[id].excl) busy_keys.erase(reqs[id].excl);
+                finish(id, AGILE_OK, 0, 0, t);
+            }
+            admitted -= s.mem;
+            admitted_pub.store(admitted);
+            s.reqs.clear();
+            s.mem = 0;
+            s.busy = false;
+        }
+    }
+
+    void launch(Slot &s, uint64_t t) {
+        if (!cfg.continuous && any_busy()) return;
+        std::vector<uint32_t> batch;
+        std::unordered_set<uint64_t> keys;
+        uint64_t mem = 0;
+        for (auto it = waiting.begin(); it != waiting.end() && batch.size() < cfg.max_batch;) {
+            const agile_request_t &r = reqs[*it];
+            if (admitted + mem + r.mem_bytes > cfg.mem_budget) break;   // admission in order
+            if (r.excl && (busy_keys.count(r.excl) || keys.count(r.excl))) { ++it; continue; }
+            batch.push_back(*it);
+            mem += r.mem_bytes;
+            if (r.excl) keys.insert(r.excl);
+            it = waiting.erase(it);
+            if (!cfg.continuous) break;
+        }
+        if (batch.empty()) return;
+        const size_t n = batch.size();
+        uint64_t *pre = reinterpret_cast<uint64_t *>(s.staging + 64 + 64 * n);
+        pre[0] = 0;
+        for (size_t i = 0; i < n; ++i) {
+            const agile_work_t &w = reqs[batch[i]].work;
+            std::memcpy(s.staging + 64 + 64 * i, &w, 64);
+            pre[i + 1] = pre[i] + (w.n + cfg.tile - 1) / cfg.tile;
+        }
+        const uint64_t hdr[8] = {n, pre[n], 0, cfg.tile, 0, 0, 0, 0};
+        std::memcpy(s.staging, hdr, 64);
+        cudaMemcpyAsync(s.dev, s.staging, 64 + 64 * n + 8 * (n + 1), cudaMemcpyHostToDevice, s.stream);
+        agile_batch_config_t bc{cfg.tile, 1, 2, 0};
+        const int rc = agile_batch_launch(s.dev, n, &bc, s.stream);
+        cudaEventRecord(s.done, s.stream);
+        const uint32_t seq = launches++;
+        for (uint32_t id : batch) {
+            comp[id].admit_ns = t;
+            comp[id].launch = seq;
+            if (reqs[id].excl) busy_keys.insert(reqs[id].excl);
+        }
+        if (rc != AGILE_OK) {                        // nothing ran: complete them with the error
+            cudaStreamSynchronize(s.stream);
+            for (uint32_t id : batch) {
+                if (reqs[id].excl) busy_keys.erase(reqs[id].excl);
+                finish(id, rc, 0, 0, now());
+            }
+            return;
+        }
+        s.reqs = std::move(batch);
+        s.mem = mem;
+        s.busy = true;
+        admitted += mem;
+        admitted_pub.store(admitted);
+        if (admitted > peak_pub.load()) peak_pub.store(admitted);
+    }
+
+    void run() {
+        cudaSetDevice(device);
+        for (;;) {
+            take_incoming();
+            uint64_t t = now();
+            reap(t);
+            while (!arrivals.empty() && arrivals.top().first <= t) {
+                const uint32_t id = arrivals.top().second;
+                arrivals.pop();
+                arrive(id, t);
+            }
+            for (Slot &s : slots)
+                if (!s.busy && !waiting.empty()) launch(s, now());
+            const bool idle = !any_busy() && waiting.empty();
+            if (stop.load() && idle && arrivals.empty()) {
+                std::lock_guard<std::mutex> g(mu_in);
+                if (incoming.empty()) break;
+                continue;
+            }
+            if (any_busy()) {
+                std::this_thread::yield();
+            } else if (!arrivals.empty()) {
+                const uint64_t next = arrivals.top().first;
+                const uint64_t t2 = now();
+                if (next > t2 + 20000) std::this_thread::sleep_for(std::chrono::nanoseconds(
+                                           std::min<uint64_t>(next - t2 - 10000, 200000)));
+            } else {
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+        }
+    }
+};
+
+extern "C" {
+
+size_t agile_worker_device_bytes(const agile_worker_config_t *cfg) {
+    if (cfg == nullptr || cfg->max_batch == 0 || cfg->max_inflight == 0) return 0;
+    return slot_bytes(cfg->max_batch) * cfg->max_inflight;
+}
+
+int agile_worker_create(const agile_worker_config_t *cfg, const agile_guard_table_t *const *h_tables,
+                        const agile_dev_table_t *const *d_tables, void *const *d_logs,
+                        size_t n_clients, void *d_buf, size_t bytes, agile_worker_t **out) {
+    if (cfg == nullptr || out == nullptr || h_tables == nullptr || d_tables == nullptr ||
+        n_clients == 0 || d_buf == nullptr)
+        return AGILE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->max_batch == 0 || cfg->max_inflight == 0 || cfg->max_inflight > 64 ||
+        cfg->tile < 512 || (cfg->tile & 511))
+        return AGILE_ERR_INVALID_ARG;
+    if (((uintptr_t)d_buf & 255) != 0) return AGILE_ERR_ALIGN;
+    if (bytes < agile_worker_device_bytes(cfg)) return AGILE_ERR_TOO_LARGE;
+    for (size_t i = 0; i < n_clients; ++i)
+        if (h_tables[i] == nullptr || d_tables[i] == nullptr) return AGILE_ERR_INVALID_ARG;
+    agile_worker *w = new (std::nothrow) agile_worker;
+    if (w == nullptr) return AGILE_ERR_NOMEM;
+    w->cfg = *cfg;
+    w->htab.assign(h_tables, h_tables + n_clients);
+    w->dtab.assign(d_tables, d_tables + n_clients);
+    w->dlog.assign(n_clients, nullptr);
+    if (d_logs) for (size_t i = 0; i < n_clients; ++i) w->dlog[i] = d_logs[i];
+    cudaGetDevice(&w->device);
+    const size_t sb = slot_bytes(cfg->max_batch);
+    w->slots.resize(cfg->max_inflight);
+    for (uint32_t k = 0; k < cfg->max_inflight; ++k) {
+        Slot &s = w->slots[k];
+        s.dev = static_cast<unsigned char *>(d_buf) + k * sb;
+        cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.staging), sb);
+        if (e != cudaSuccess) {
+            agile::set_cuda_error((int)e, "worker slot");
+            agile_worker_destroy(w);
+            return AGILE_ERR_CUDA;
+        }
+    }
+    *out = w;
+    return AGILE_OK;
+}
+
+int agile_worker_submit(agile_worker_t *w, const agile_request_t *reqs, size_t n) {
+    if (w == nullptr || (n > 0 && reqs == nullptr)) return AGILE_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> g(w->mu_in);
+        w->incoming.insert(w->incoming.end(), reqs, reqs + n);
+    }
+    w->submitted.fetch_add(n);
+    return AGILE_OK;
+}
+
+int agile_worker_start(agile_worker_t *w) {
+    if (w == nullptr || w->started.exchange(true)) return AGILE_ERR_INVALID_ARG;
+    w->t0 = std::chrono::steady_clock::now();
+    w->th = std::thread([w] { w->run(); });
+    return AGILE_OK;
+}
+
+int agile_worker_poll(agile_worker_t *w, agile_completion_t *out, size_t cap, size_t *got,
+                      uint32_t wait_ms) {
+    if (w == nullptr || got == nullptr || (cap > 0 && out == nullptr)) return AGILE_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(w->mu_out);
+    if (w->ready.empty() && wait_ms > 0)
+        w->cv_out.wait_for(lk, std::chrono::milliseconds(wait_ms), [w] { return !w->ready.empty(); });
+    size_t k = 0;
+    while (k < cap && !w->ready.empty()) {
+        out[k++] = w->ready.front();
+        w->ready.pop_front();
+    }
+    *got = k;
+    return AGILE_OK;
+}
+
+int agile_worker_clock(agile_worker_t *w, uint64_t *now_ns, uint64_t *admitted_bytes,
+                       uint64_t *peak_admitted_bytes) {
+    if (w == nullptr) return AGILE_ERR_INVALID_ARG;
+    if (now_ns) *now_ns = w->started.load() ? w->now() : 0;
+    if (admitted_bytes) *admitted_bytes = w->admitted_pub.load();
+    if (peak_admitted_bytes) *peak_admitted_bytes = w->peak_pub.load();
+    return AGILE_OK;
+}
+
+void agile_worker_destroy(agile_worker_t *w) {
+    if (w == nullptr) return;
+    w->stop.store(true);
+    if (w->th.joinable()) w->th.join();
+    for (Slot &s : w->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.staging) cudaFreeHost(s.staging);
+    }
+    delete w;
+}
+
+}  // extern "C"
