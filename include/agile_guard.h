@@ -115,6 +115,10 @@ typedef struct {
     uint64_t bytes;           /* size of the device buffer in use                       */
     uint32_t search_steps;    /* binary-search steps that cover any page's range slice  */
     uint32_t reserved;
+    const uint32_t *crange;   /* windows under 4 GiB: n records of 4 u32 {start - lo,
+                                 last byte - lo, rank (0 MMIO, 1 protected, 2 user), id};
+                                 else NULL                                              */
+    const void *reserved2;
 } agile_dev_table_t;
 
 /* Decoded violation log. The first fault is the violating access with the smallest

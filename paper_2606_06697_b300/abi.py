@@ -42,7 +42,9 @@ class _DevTable(ctypes.Structure):
                 ("page", ctypes.c_void_p), ("base", ctypes.c_void_p), ("end", ctypes.c_void_p),
                 ("kind", ctypes.c_void_p), ("id", ctypes.c_void_p),
                 ("zero_page", ctypes.c_void_p), ("sink_page", ctypes.c_void_p),
-                ("bytes", ctypes.c_uint64)]
+                ("bytes", ctypes.c_uint64), ("search_steps", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("crange", ctypes.c_void_p),
+                ("reserved2", ctypes.c_void_p)]
 
 
 class _Record(ctypes.Structure):

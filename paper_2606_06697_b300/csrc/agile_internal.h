@@ -19,6 +19,8 @@ struct agile_guard_table {
     uint32_t search_steps = 0;            // steps covering the largest page slice
     std::vector<unsigned char> staging;   // host image of the device buffer
     size_t off_base = 0, off_end = 0, off_kind = 0, off_id = 0, total = 0;
+    bool compact = false;                 // window < 4 GiB: packed 32-bit records exist
+    size_t off_crange = 0;
 };
 
 namespace agile {

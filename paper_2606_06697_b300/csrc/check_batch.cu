@@ -7,8 +7,10 @@
 // bytes as one 8-byte load and writes 8 verdict bytes as one 8-byte store. The whole
 // table (page map and range arrays) is staged into shared memory by bulk copies when it
 // fits in 96 KiB, so the classification -- page lookup, and a short binary search on
-// mixed pages -- runs inline on shared memory. Each thread keeps its smallest violation
-// in registers; the block reduces them once at the end.
+// mixed pages -- runs inline on shared memory; tables whose window spans under 4 GiB
+// stage 32-bit copies of the range bounds instead and decide allowed accesses in 32-bit
+// arithmetic. Each thread keeps its smallest violation in registers; the block reduces
+// them once at the end.
 #include <cuda_runtime.h>
 
 #include "agile_internal.h"
@@ -22,40 +24,76 @@ using agile::TView;
 
 constexpr int kThreads = 512;
 
-// Branch-light form of the rule for random access streams: every lane reads its page
-// entry and runs the same fixed number of binary-search steps over its page's range
-// slice, and the allow decision is made with selects, so a warp stays converged on the
-// common path. An access allowed by its page entry (all-user page) or by the range the
-// search lands on is decided here; everything else -- denials, accesses across the
-// window edge, illegal widths -- takes the full classification out of line.
-__device__ __forceinline__ bool allow_uniform(const TView &V, uint64_t a, uint32_t w) {
+// Uniform decision in 32-bit arithmetic, for tables whose window spans under 4 GiB (the
+// packed records hold each range's start and last byte as offsets from the window start,
+// its kind and id). Every lane runs the same steps: the page entry, the fixed-step search
+// for the last range starting at or below the access, then the three ranges around that
+// point -- that range and the next two -- tested with selects. Allowed when the first holds
+// the whole access; otherwise the touched ranges' class (MMIO, then protected, then user,
+// the lowest-based range of that class reported) or unmapped. Returns false -- leaving the
+// full rule to decide -- when a fourth range may be touched or the access crosses the
+// window's lower edge. A warp therefore runs one path per access whatever mix of
+// verdicts its lanes see.
+__device__ __forceinline__ bool decide32(const TView &V, uint64_t a, uint32_t w, uint32_t *v,
+                                         uint32_t *rid) {
     const uint64_t off = a - V.lo;
-    const bool inwin = (off >> V.lg) < V.npages;
-    const uint32_t p = inwin ? (uint32_t)(off >> V.lg) : 0u;
-    const uint32_t e = V.page[p], e2 = V.page[p + 1];
-    const uint32_t f = e & agile::kIdxMask, f2 = e2 & agile::kIdxMask;
-    const bool fast = inwin && (e >> 30) == agile::PG_USER && (off & V.gmask) + w <= V.gmask + 1;
-    const uint32_t hi = f2 + 1 < V.n ? f2 + 1 : V.n;
-    uint32_t b = f, len = (inwin && hi > f) ? hi - f : 0u;
+    if (off > V.last - V.lo) {                       // outside the window
+        if (a < V.lo && a + w > V.lo) return false;  // reaches into it
+        *v = AGILE_DENY_UNMAPPED;
+        *rid = agile::kNoRange;
+        return true;
+    }
+    const uint32_t o = (uint32_t)off;
+    const uint64_t oe = (uint64_t)o + w - 1;         // last byte, relative
+    const uint32_t p = o >> V.lg;
+    const uint32_t n = V.n;
+    const uint32_t f = V.page[p] & agile::kIdxMask, f2 = V.page[p + 1] & agile::kIdxMask;
+    const uint32_t hi = f2 + 1 < n ? f2 + 1 : n;
+    uint32_t b = f, len = hi - f;
     for (uint32_t it = 0; it < V.steps; ++it) {
         const uint32_t half = len >> 1;
-        const uint32_t probe = b + half < V.n ? b + half : (V.n ? V.n - 1 : 0u);
-        const bool le = len > 0 && V.base[probe] <= a;
+        const uint32_t probe = b + half < n ? b + half : n - 1;
+        const bool le = len > 0 && V.crange[probe].x <= o;
         b = le ? b + half + 1 : b;
         len = le ? len - half - 1 : half;
     }
-    const uint32_t j = b > f ? b - 1 : 0u;          // index 0 exists (npages > 0 implies n > 0)
-    const bool hit = b > f && V.kind[j] == AGILE_USER && V.end[j] >= a + w;   // base[j] <= a
-    return fast || hit;
+    const bool v0 = b > 0, v1 = b < n, v2 = b + 1 < n, v3 = b + 2 < n;
+    const uint4 r0 = V.crange[v0 ? b - 1 : 0];
+    const uint4 r1 = V.crange[v1 ? b : 0];
+    const uint4 r2 = V.crange[v2 ? b + 1 : 0];
+    const uint32_t s3 = V.crange[v3 ? b + 2 : 0].x;
+    if (v3 && (uint64_t)s3 <= oe) return false;      // a fourth range may be touched
+    const bool t0 = v0 && r0.y >= o;                 // r0 starts at or below o
+    const bool t1 = v1 && (uint64_t)r1.x <= oe;      // r1, r2 start above o
+    const bool t2 = v2 && (uint64_t)r2.x <= oe;
+    // .z is the deny rank: 0 MMIO, 1 protected, 2 user
+    if (t0 && r0.z == 2u && (uint64_t)r0.y >= oe) {
+        *v = AGILE_ALLOW;
+        *rid = r0.w;
+        return true;
+    }
+    uint32_t best = t0 ? r0.z : 3u, id = r0.w;
+    id = (t1 && r1.z < best) ? r1.w : id;
+    best = (t1 && r1.z < best) ? r1.z : best;
+    id = (t2 && r2.z < best) ? r2.w : id;
+    best = (t2 && r2.z < best) ? r2.z : best;
+    *v = (0x04030102u >> (8 * best)) & 0xFFu;        // rank 0..3 -> MMIO, PROTECTED, STRADDLE, UNMAPPED
+    *rid = best == 3 ? agile::kNoRange : id;
+    return true;
 }
 
-__device__ __forceinline__ uint32_t check_one(const TView &V, uint64_t a, uint32_t w, size_t i,
-                                              LaneLog &ll) {
-    const bool legal = w != 0 && w <= 16 && (w & (w - 1)) == 0 && a <= ~0ull - w;
-    if (legal && V.npages > 0 && allow_uniform(V, a, w)) return AGILE_ALLOW;
-    uint32_t rid = agile::kNoRange;
-    const uint32_t v = (w != 0 && w <= 16 && (w & (w - 1)) == 0)
-                           ? agile::classify_slow(V, a, w, &rid) : (uint32_t)AGILE_DENY_INVALID;
+__device__ __forceinline__ bool legal_width(uint32_t w) {
+    return w <= 16 && ((0x10116u >> w) & 1u);        // 1, 2, 4, 8, 16
+}
+
+// Full rule for one access (for the accesses the uniform decision leaves open).
+template <bool C32>
+__device__ __forceinline__ uint32_t full_one(const TView &V, uint64_t a, uint32_t w, size_t i,
+                                             LaneLog &ll) {
+    uint32_t rid = agile::kNoRange, v;
+    if (!legal_width(w)) v = AGILE_DENY_INVALID;
+    else if constexpr (C32) v = agile::classify_slow(V, a, w, &rid);
+    else v = agile::classify(V, a, w, &rid);
     if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
     return v;
 }
@@ -73,9 +111,10 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
     const size_t ngroups = n / VEC;
 
+    constexpr bool kC32 = MODE == agile::STAGE_COMPACT;
     LaneLog ll;
     for (size_t g = tid; g < ngroups; g += nthreads) {
-        if constexpr (VEC == 8) {
+        if constexpr (VEC == 8 && kC32) {
             const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
             uint64_t av[8];
 #pragma unroll
@@ -86,19 +125,48 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             }
             const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
             uint64_t out = 0;
+            uint32_t open = 0;                         // accesses left to the full rule
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
-                out |= (uint64_t)check_one(V, av[k], w, g * 8 + k, ll) << (8 * k);
+                uint32_t v = 0, rid = agile::kNoRange;
+                const bool done = legal_width(w) && av[k] <= ~0ull - w && decide32(V, av[k], w, &v, &rid);
+                open |= (uint32_t)!done << k;
+                if (done && v != AGILE_ALLOW) ll.note(g * 8 + k, agile::pack_info(0, v, w, rid), av[k]);
+                out |= (uint64_t)v << (8 * k);
+            }
+#pragma unroll 1
+            for (; open; open &= open - 1) {           // rare: re-read the access, full rule
+                const int k = __ffs(open) - 1;
+                const size_t i = g * 8 + k;
+                const uint64_t v = full_one<true>(V, addr[i], width[i], i, ll);
+                out = (out & ~(0xFFull << (8 * k))) | v << (8 * k);
+            }
+            __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), (unsigned long long)out);
+        } else if constexpr (VEC == 8) {
+            const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
+            uint64_t av[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint4 q = __ldcs(pa + k);
+                av[2 * k] = (uint64_t)q.y << 32 | q.x;
+                av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
+            }
+            const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
+            uint64_t out = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
+                out |= (uint64_t)full_one<false>(V, av[k], w, g * 8 + k, ll) << (8 * k);
             }
             __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), (unsigned long long)out);
         } else {
-            verdict[g] = (uint8_t)check_one(V, addr[g], width[g], g, ll);
+            verdict[g] = (uint8_t)full_one<kC32>(V, addr[g], width[g], g, ll);
         }
     }
     if (VEC > 1 && blockIdx.x == 0 && threadIdx.x < 32) {    // the last n % VEC accesses
         const size_t i = ngroups * VEC + threadIdx.x;
-        if (i < n) verdict[i] = (uint8_t)check_one(V, addr[i], width[i], i, ll);
+        if (i < n) verdict[i] = (uint8_t)full_one<kC32>(V, addr[i], width[i], i, ll);
     }
     agile::block_log_flush(log, ll);
 }
@@ -123,7 +191,8 @@ int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size
 template <int VEC>
 int launch_mode(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
                 uint8_t *v, LogDev *log, cudaStream_t st) {
-    switch (agile::stage_mode(T, true)) {
+    switch (agile::stage_mode(T, true, true)) {
+        case agile::STAGE_COMPACT: return launch<agile::STAGE_COMPACT, VEC>(T, a, w, n, v, log, st);
         case agile::STAGE_ALL: return launch<agile::STAGE_ALL, VEC>(T, a, w, n, v, log, st);
         case agile::STAGE_PAGES: return launch<agile::STAGE_PAGES, VEC>(T, a, w, n, v, log, st);
         default: return launch<agile::STAGE_NONE, VEC>(T, a, w, n, v, log, st);

@@ -69,12 +69,14 @@ struct TView {
     const uint32_t *page;
     const uint64_t *base, *end;
     const uint32_t *kind, *id;
+    const uint4 *crange;        // {start - lo, last - lo, rank, id} (windows under 4 GiB), or NULL
 };
 
 __device__ __forceinline__ TView view_of(const agile_dev_table_t &T) {
     const uint64_t G = 1ull << T.log2_page;
     return TView{T.lo, T.npages, G - 1, T.lo + (T.npages << T.log2_page) - 1, T.log2_page, T.n,
-                 T.search_steps, T.page, T.base, T.end, T.kind, T.id};
+                 T.search_steps, T.page, T.base, T.end, T.kind, T.id,
+                 reinterpret_cast<const uint4 *>(T.crange)};
 }
 
 __device__ __forceinline__ uint32_t deny_of_kind(uint32_t kind) {
@@ -297,7 +299,7 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
 
 // Shared-memory staging modes chosen by the host: nothing, the page map, or the page map
 // and the range arrays.
-enum : int { STAGE_NONE = 0, STAGE_PAGES = 1, STAGE_ALL = 2 };
+enum : int { STAGE_NONE = 0, STAGE_PAGES = 1, STAGE_ALL = 2, STAGE_COMPACT = 3 };
 
 __host__ __device__ inline uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
@@ -306,6 +308,7 @@ __host__ __device__ inline uint32_t stage_bytes(const agile_dev_table_t &T, int 
     if (mode == STAGE_NONE) return 0;
     uint32_t b = round16((T.npages + 1) * 4);
     if (mode == STAGE_ALL) b += 2 * round16(T.n * 8ull) + 2 * round16(T.n * 4ull);
+    if (mode == STAGE_COMPACT) b += round16(T.n * 16ull);       // packed records
     return b;
 }
 
@@ -334,6 +337,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     uint64_t *s_end = reinterpret_cast<uint64_t *>(smem + pb + bb);
     uint32_t *s_kind = reinterpret_cast<uint32_t *>(smem + pb + 2 * bb);
     uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + pb + 2 * bb + kb);
+    uint4 *s_cr = reinterpret_cast<uint4 *>(smem + pb);                 // STAGE_COMPACT layout
     const uint32_t bar = smem_addr(s_bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -341,7 +345,8 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t total = MODE == STAGE_ALL ? pb + 2 * bb + 2 * kb : pb;
+        const uint32_t total = MODE == STAGE_ALL ? pb + 2 * bb + 2 * kb
+                             : MODE == STAGE_COMPACT ? pb + round16(T.n * 16ull) : pb;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total)
                      : "memory");
         bulk_g2s(s_page, T.page, pb, bar);
@@ -351,6 +356,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
             bulk_g2s(s_kind, T.kind, kb, bar);
             bulk_g2s(s_id, T.id, kb, bar);
         }
+        if (MODE == STAGE_COMPACT && T.n > 0) bulk_g2s(s_cr, T.crange, round16(T.n * 16ull), bar);
     }
     if (!mbar_wait(bar, 0)) {               // (block-uniform only by timing: any thread may)
         if (log != nullptr && threadIdx.x == 0) atomicOr(&log->status, AGILE_LOG_STATUS_TIMEOUT);
@@ -360,12 +366,16 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
             for (uint32_t i = threadIdx.x; i < T.n; i += blockDim.x) {
                 s_base[i] = T.base[i]; s_end[i] = T.end[i]; s_kind[i] = T.kind[i]; s_id[i] = T.id[i];
             }
+        if (MODE == STAGE_COMPACT)
+            for (uint32_t i = threadIdx.x; i < T.n; i += blockDim.x)
+                s_cr[i] = reinterpret_cast<const uint4 *>(T.crange)[i];
     }
     __syncthreads();
     V.page = s_page;
     if constexpr (MODE == STAGE_ALL) {
         V.base = s_base; V.end = s_end; V.kind = s_kind; V.id = s_id;
     }
+    if constexpr (MODE == STAGE_COMPACT) V.crange = s_cr;
     return V;
 }
 
@@ -418,8 +428,11 @@ __device__ inline void slots_flush(LogDev *L, WarpSlots &S) {
 }
 
 // Host side: pick the staging mode for a table (96 KiB for everything, 48 KiB for pages).
-inline int stage_mode(const agile_dev_table_t &T, bool want_ranges) {
+// want_compact: the kernel has a 32-bit path and the table carries the compact arrays.
+inline int stage_mode(const agile_dev_table_t &T, bool want_ranges, bool want_compact = false) {
     if (T.npages == 0) return STAGE_NONE;
+    if (want_compact && T.crange != nullptr && stage_bytes(T, STAGE_COMPACT) <= 96 * 1024)
+        return STAGE_COMPACT;
     if (want_ranges && stage_bytes(T, STAGE_ALL) <= 96 * 1024) return STAGE_ALL;
     if (stage_bytes(T, STAGE_PAGES) <= 48 * 1024) return STAGE_PAGES;
     return STAGE_NONE;

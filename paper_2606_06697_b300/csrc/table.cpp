@@ -133,6 +133,14 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
         t->off_end = off;  off += align256(n * 8);
         t->off_kind = off; off += align256(n * 4);
         t->off_id = off;   off += align256(n * 4);
+        // Windows under 4 GiB also get one packed 16-byte record per range -- start and
+        // last byte as 32-bit offsets from lo, kind, id -- so a kernel can decide in 32 bits
+        // with one 128-bit load per range.
+        t->compact = n > 0 && lg <= 31 && t->npages <= ((1ull << 32) - 1) >> lg;
+        if (t->compact) {
+            t->off_crange = off;
+            off += align256(n * 16);
+        }
         t->total = off;
         t->staging.assign(t->total, 0);
         std::memcpy(t->staging.data() + kPageOff, t->page.data(), t->page.size() * 4);
@@ -141,6 +149,16 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
             std::memcpy(t->staging.data() + t->off_end, t->end.data(), n * 8);
             std::memcpy(t->staging.data() + t->off_kind, t->kind.data(), n * 4);
             std::memcpy(t->staging.data() + t->off_id, t->id.data(), n * 4);
+        }
+        if (t->compact) {
+            uint32_t *cr = reinterpret_cast<uint32_t *>(t->staging.data() + t->off_crange);
+            for (size_t i = 0; i < n; ++i) {
+                cr[4 * i] = (uint32_t)(t->base[i] - t->lo);
+                cr[4 * i + 1] = (uint32_t)(t->end[i] - 1 - t->lo);
+                // deny rank of the kind: 0 MMIO, 1 protected, 2 user (also "allowable")
+                cr[4 * i + 2] = t->kind[i] == AGILE_MMIO ? 0u : t->kind[i] == AGILE_PROTECTED ? 1u : 2u;
+                cr[4 * i + 3] = t->id[i];
+            }
         }
     } catch (const std::bad_alloc &) {
         delete t;
@@ -185,6 +203,7 @@ int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, 
     h.sink_page = d + kSinkOff;
     h.bytes = t->total;
     h.search_steps = t->search_steps;
+    if (t->compact) h.crange = (const uint32_t *)(d + t->off_crange);
     static_assert(sizeof(agile_dev_table_t) <= kHeaderBytes, "header fits");
     std::memcpy(t->staging.data(), &h, sizeof h);
     std::memset(t->staging.data() + kZeroOff, 0, 128);

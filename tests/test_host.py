@@ -123,3 +123,29 @@ def test_upload_without_gpu_reports_cuda_error():
     with pytest.raises(ag.AgileError) as e:
         t.upload(0x100000)
     assert e.value.code in (-7,)
+
+
+def test_python_struct_mirrors_match_the_header():
+    """ctypes mirrors of the public structs have the sizes the C header gives them."""
+    import ctypes
+    from paper_2606_06697_b300 import abi
+    src = r"""
+#include <stdio.h>
+#include "agile_guard.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu ", sizeof(agile_range_t), sizeof(agile_dev_table_t),
+         sizeof(agile_violation_record_t), sizeof(agile_work_t), sizeof(agile_batch_config_t),
+         sizeof(agile_request_t), sizeof(agile_completion_t), sizeof(agile_worker_config_t));
+  return 0;
+}
+"""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "s")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    mirrors = [abi._Range, abi._DevTable, abi._Record, abi.Work, abi.BatchConfig, abi.Request,
+               abi.Completion, abi.WorkerConfig]
+    assert sizes == [ctypes.sizeof(m) for m in mirrors]
