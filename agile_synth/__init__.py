@@ -560,3 +560,33 @@ def serve_requests(layouts, rate: float, n: int, seed: int = SEED_BASE + 5,
             req.update(bad=kind, bad_arg=j)
         out.append(req)
     return out
+
+
+def zipf_torch(generator, s: float, n_max: int, count: int, device):
+    """Zipf(s) ranks in [1, n_max] by the same rejection-inversion method as `zipf`, drawn
+    on a device with torch (float64), for index arrays too large to draw on the host. The
+    stream comes from the torch generator, so the values differ from `zipf`'s."""
+    import torch
+    one_m_s = 1.0 - s
+
+    def H(x):
+        return torch.pow(x, one_m_s) / one_m_s
+
+    def H_inv(y):
+        return torch.pow(y * one_m_s, 1.0 / one_m_s)
+
+    t = lambda v: torch.tensor(v, dtype=torch.float64, device=device)
+    h_x1 = H(t(1.5)) - 1.0
+    h_n = H(t(n_max + 0.5))
+    squeeze = 2.0 - H_inv(H(t(2.5)) - 2.0 ** (-s))
+    out = torch.empty(count, dtype=torch.int64, device=device)
+    todo = torch.arange(count, device=device)
+    while todo.numel():
+        u = h_n + torch.rand(todo.numel(), dtype=torch.float64, generator=generator,
+                             device=device) * (h_x1 - h_n)
+        x = H_inv(u)
+        k = torch.clamp(torch.floor(x + 0.5), 1, n_max)
+        ok = (k - x <= squeeze) | (u >= H(k + 0.5) - torch.pow(k, -s))
+        out[todo[ok]] = k[ok].to(torch.int64)
+        todo = todo[~ok]
+    return out

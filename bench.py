@@ -294,7 +294,8 @@ def run_ours(args, ws, rank, local):
 
     # the same kernels from hand-written PTX through the guard pass (poison)
     ptx_kern = ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C)
-    ptx_gbs = STEP_BYTES / (sum(ptx_kern.values()) / 1e3) / 1e9
+    ptx_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("guarded")) / 1e3) / 1e9
+    ptx_plain_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("plain")) / 1e3) / 1e9
 
     # dominant kernel roofline
     top = max(kern, key=kern.get)
@@ -306,6 +307,7 @@ def run_ours(args, ws, rank, local):
 
     # batch check throughput: the 1M-access table workload and a 2^28-access stream
     batch = batch_throughput(ag, torch, dev, stream)
+    irregular = irregular_sweep(ag, torch, dev, stream)
     clients = batch_clients(ag, torch, dev, stream)
     serving = serve_sweep(ag, torch, dev)
 
@@ -356,10 +358,11 @@ def run_ours(args, ws, rank, local):
                        "page_bytes": 1 << 21, "policy": "poison",
                        "l2": "each array 1 GiB, larger than the 126 MB L2; no flush needed"},
             "unguarded_gbs": value_u, "guarded_over_unguarded": value / ws / value_u,
-            "ptx_injected_gbs": ptx_gbs, "ptx_injected_kernel_ms": ptx_kern,
+            "ptx_injected_gbs": ptx_gbs, "ptx_plain_gbs": ptx_plain_gbs,
+            "ptx_injected_over_plain": ptx_gbs / ptx_plain_gbs, "ptx_kernel_ms": ptx_kern,
             "kernel_ms": {f"{op}_guarded": kern[op] for op in ops} |
                          {f"{op}_unguarded": kern_u[op] for op in ops},
-            "roofline": roofline, "batch_check": batch, "batch_clients": clients, "serving": serving,
+            "roofline": roofline, "batch_check": batch, "irregular": irregular, "batch_clients": clients, "serving": serving,
             "e2e": e2e,
             "gpu_launches": args.steps * 4, "clocks": ck, "cpu_baseline": cpu,
         }
@@ -367,32 +370,36 @@ def run_ours(args, ws, rank, local):
 
 
 def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):
-    """Mean kernel time of the PTX-instrumented copy/scale/triad (poison), CUDA events."""
+    """Mean kernel time of the hand-written PTX copy/scale/triad, instrumented by the guard
+    pass (poison) and as written (no guard), CUDA events."""
     import ctypes
-    text, _ = ag.agile_guard_instrument_ptx(open(PTX_STREAM).read(), "poison")
-    mod = ag.agile_module_load(text)
+    src = open(PTX_STREAM).read()
+    guarded = ag.agile_module_load(ag.agile_guard_instrument_ptx(src, "poison")[0])
+    plain = ag.agile_module_load(src)
     ag.agile_violation_log_init(log, 0, stream)
-    ag.agile_module_bind(mod, dtab, log, stream)
+    ag.agile_module_bind(guarded, dtab, log, stream)
     grid = torch.cuda.get_device_properties(dev).multi_processor_count * 4
     args = [ctypes.c_uint64(A.data_ptr()), ctypes.c_uint64(B.data_ptr()),
             ctypes.c_uint64(C.data_ptr()), ctypes.c_uint64(N_ELEMS), ctypes.c_float(3.0)]
     out = {}
-    for op in ("copy", "scale", "triad"):
-        for _ in range(3):
-            ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, 512, args, stream)
-        evs = []
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, 512, args, stream)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        out[op] = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    for name, mod in (("guarded", guarded), ("plain", plain)):
+        for op in ("copy", "scale", "triad"):
+            for _ in range(3):
+                ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, 512, args, stream)
+            evs = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, 512, args, stream)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            out[f"{op}_{name}"] = statistics.mean(a.elapsed_time(b) for a, b in evs)
     rc, rec = ag.agile_violation_log_read(log, stream)
     assert rc == 0 and rec.count == 0, "violation in the PTX-injected run"
-    mod.unload()
+    guarded.unload()
+    plain.unload()
     return out
 
 
@@ -442,6 +449,86 @@ def batch_clients(ag, torch, dev, stream, n_clients=256, reps=5):
             "separate_gbs": nbytes / ms_sep / 1e6, "graph_gbs": nbytes / ms_graph / 1e6,
             "speedup_graph_vs_separate": ms_sep / ms_graph,
             "mix": {o: sum(1 for s_ in specs if s_["op"] == o) for o in ("copy", "gather", "hist")}}
+
+
+
+def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5):
+    """Gather / scatter / histogram over the 16 GiB striped table (4096 user allocations of
+    4 MiB, each followed by a 64 KiB protected range), 2^28 int64 indices, uniform and
+    Zipf(1.1), 0.1% aimed into protected ranges; guarded (poison, 2 MiB and 64 KiB pages)
+    against unguarded. Indices are drawn on the device with a seeded torch generator."""
+    r, span, off = syn.irregular_layout(n)
+    stripes, ue = 4096, (4 << 20) // 4
+    se, pe, bins = ((4 << 20) + (64 << 10)) // 4, (64 << 10) // 4, 1 << 20
+    arena = torch.empty(span, dtype=torch.uint8, device=dev)
+    base = arena.data_ptr()
+    g = torch.Generator(device=dev).manual_seed(syn.SEED_BASE + 3)
+    arena[:off["bins"]].view(torch.float32).uniform_(1, 2, generator=g)
+    idx = arena[off["idx"]:off["idx"] + 8 * n].view(torch.int64)
+    out_t = arena[off["out"]:off["out"] + 4 * n].view(torch.float32)
+    bins_t = arena[off["bins"]:off["bins"] + 4 * bins].view(torch.int32)
+    rr = r.shifted(base)
+    tabs = {}
+    for lg in (21, 16):
+        t = ag.agile_guard_table_build(rr.base, rr.size, rr.kind, rr.ident, lg)
+        b = torch.empty(t.device_bytes(), dtype=torch.uint8, device=dev)
+        tabs[lg] = (t, b, t.upload(b, stream))
+    log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
+    useful = {"gather": 16, "scatter": 12, "hist": 8}
+    res = {}
+    for dist in ("uniform", "zipf"):
+        if dist == "uniform":
+            rank = torch.randint(0, stripes * ue, (n,), generator=g, device=dev, dtype=torch.int64)
+        else:
+            k = syn.zipf_torch(g, 1.1, stripes * ue, n, dev) - 1
+            rank = (k * syn.ODD_MIX) & (stripes * ue - 1)
+        element = (rank // ue) * se + rank % ue
+        key = rank & (bins - 1)
+        bad = torch.unique(torch.randint(0, n, (n // 1000,), generator=g, device=dev))
+        nb = bad.numel()
+        element[bad] = torch.randint(0, stripes, (nb,), generator=g, device=dev) * se + ue + \
+            torch.randint(0, pe, (nb,), generator=g, device=dev)
+        key[bad] = bins + torch.randint(0, pe, (nb,), generator=g, device=dev)
+        del rank
+        for kind in ("gather", "scatter", "hist"):
+            idx.copy_(key if kind == "hist" else element)
+            target = base + (off["bins"] if kind == "hist" else 0)
+            row = {}
+            for label, lg in (("unguarded", None), ("guarded_2MiB", 21), ("guarded_64KiB", 16)):
+                dtab = tabs[lg][2] if lg else None
+
+                def once():
+                    if lg:
+                        ag.agile_violation_log_init(log, 0, stream)
+                    ag.agile_irregular_launch(kind, dtab, idx, target, out_t, n, "poison",
+                                              log if lg else None, stream)
+                if kind == "hist":
+                    bins_t.zero_()
+                once()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                ts = []
+                for _ in range(reps):
+                    e0.record(stream)
+                    once()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                cell = {"ms": ms, "useful_gbs": useful[kind] * n / ms / 1e6}
+                if lg:
+                    rc, rec = ag.agile_violation_log_read(log, stream)
+                    assert rec.count == nb, (kind, dist, rec.count, nb)
+                    cell["violations"] = rec.count
+                row[label] = cell
+            row["guarded_over_unguarded"] = row["unguarded"]["ms"] / min(
+                row["guarded_2MiB"]["ms"], row["guarded_64KiB"]["ms"])
+            res[f"{kind}_{dist}"] = row
+        del element, key
+    del arena
+    torch.cuda.empty_cache()
+    return res
 
 
 def serve_sweep(ag, torch, dev, rates=(1e3, 3e3, 1e4, 3e4, 1e5), window_s=0.3):

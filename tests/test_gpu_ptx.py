@@ -16,7 +16,8 @@ from test_gpu_stream import _fill, _hostile_layout
 pytestmark = pytest.mark.gpu
 STREAM = open(os.path.join(os.path.dirname(ag.library_path), "ptx", "stream.ptx")).read()
 # site numbering of the hand-written kernels -> the oracle's (vector and tail share sites)
-SITE_MAP = {"copy": [0, 1, 0, 1], "scale": [0, 1, 0, 1], "triad": [0, 1, 2, 0, 1, 2]}
+SITE_MAP = {"copy": [0, 0, 1, 1, 0, 1, 0, 1], "scale": [0, 0, 1, 1, 0, 1, 0, 1],
+            "triad": [0, 0, 1, 1, 2, 2, 0, 1, 2, 0, 1, 2]}
 
 
 def launch(mod, op, A, B, C, n, s=3.0, grid=148 * 4, block=256):

@@ -40,30 +40,31 @@ def sites(text):
 @pytest.mark.parametrize("policy", ["poison", "sink", "report", "trap"])
 def test_stream_kernels_every_access_guarded(policy):
     out, rep = ag.agile_guard_instrument_ptx(STREAM, policy)
-    assert rep == {"functions": 3, "guarded": 14, "generic_guarded": 0, "skipped": 0}
+    n_acc = len(re.findall(r"\b(?:ld|st)\.global\.", STREAM))
+    assert rep == {"functions": 3, "guarded": n_acc, "generic_guarded": 0, "skipped": 0}
     s = sites(out)
-    assert len(s) == 14
-    assert [x[1] for x in s[:4]] == ["ld.global.v4.f32", "st.global.v4.f32", "ld.global.f32",
-                                     "st.global.f32"]
-    assert [int(x[2]) for x in s[:4]] == [16, 16, 4, 4]
-    assert out.count("call (__agret), __agile_guard_check") == 14
-    # every original global access now follows a guard: none keeps its own address form
-    assert not re.search(r"(ld|st)\.global\.(v4\.)?f32[^;]*\[%rd1[0-9]\]", out) or policy in ("report", "trap")
+    assert len(s) == n_acc == 28
+    assert [x[1] for x in s[:6]] == ["ld.global.v4.f32", "ld.global.v4.f32", "st.global.v4.f32",
+                                     "st.global.v4.f32", "ld.global.v4.f32", "st.global.v4.f32"]
+    assert [int(x[2]) for x in s[:8]] == [16, 16, 16, 16, 16, 16, 4, 4]
+    assert out.count("call (__agret), __agile_guard_check") == n_acc
+    loads = sum(1 for x in s if x[1].startswith("ld."))
+    stores = n_acc - loads
     if policy == "trap":
-        assert out.count("@!%__agp3 trap;") == 14
+        assert out.count("@!%__agp3 trap;") == n_acc
     else:
         assert "trap;" not in out
     if policy == "poison":
-        assert out.count("selp.b64 %__agd5, %__agd0, %__agT3, %__agp3") == 8   # loads -> zero page
-        assert out.count("@%__agp4 st.global") == 6                             # stores predicated
+        assert out.count("selp.b64 %__agd5, %__agd0, %__agT3, %__agp3") == loads   # zero page
+        assert out.count("@%__agp4 st.global") == stores                            # predicated
     if policy == "sink":
-        assert out.count("selp.b64 %__agd5, %__agd0, %__agT4, %__agp3") == 6   # stores -> sink
+        assert out.count("selp.b64 %__agd5, %__agd0, %__agT4, %__agp3") == stores  # sink page
     assemble(out)
 
 
 def test_skip_list_leaves_trusted_functions_alone():
     out, rep = ag.agile_guard_instrument_ptx(STREAM, "poison", skip=["agile_ptx_copy"])
-    assert rep["guarded"] == 10 and rep["skipped"] == 4 and rep["functions"] == 3
+    assert rep["guarded"] == 20 and rep["skipped"] == 8 and rep["functions"] == 3
     body = out[out.index(".entry agile_ptx_copy"):out.index(".entry agile_ptx_scale")]
     assert "agile guard" not in body and "__agT" not in body
     assemble(out)
