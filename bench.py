@@ -289,13 +289,18 @@ def run_ours(args, ws, rank, local):
         return
 
     # unguarded twins
-    ms_u, kern_u = timed(False, max(args.steps // 2, 10), 3, per_kernel=True)
-    value_u = STEP_BYTES * max(args.steps // 2, 10) / (ms_u / 1e3) / 1e9
+    if "unguarded" in args.legs:
+        ms_u, kern_u = timed(False, max(args.steps // 2, 10), 3, per_kernel=True)
+        value_u = STEP_BYTES * max(args.steps // 2, 10) / (ms_u / 1e3) / 1e9
+    else:
+        kern_u, value_u = {op: None for op in ops}, None
 
     # the same kernels from hand-written PTX through the guard pass (poison)
-    ptx_kern = ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C)
-    ptx_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("guarded")) / 1e3) / 1e9
-    ptx_plain_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("plain")) / 1e3) / 1e9
+    ptx_kern, ptx_gbs, ptx_plain_gbs = None, None, None
+    if "ptx" in args.legs:
+        ptx_kern = ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C)
+        ptx_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("guarded")) / 1e3) / 1e9
+        ptx_plain_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("plain")) / 1e3) / 1e9
 
     # dominant kernel roofline
     top = max(kern, key=kern.get)
@@ -306,41 +311,18 @@ def run_ours(args, ws, rank, local):
                 "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)"}
 
     # batch check throughput: the 1M-access table workload and a 2^28-access stream
-    batch = batch_throughput(ag, torch, dev, stream)
-    irregular = irregular_sweep(ag, torch, dev, stream)
-    clients = batch_clients(ag, torch, dev, stream)
-    serving = serve_sweep(ag, torch, dev)
+    batch = batch_throughput(ag, torch, dev, stream) if "batch" in args.legs else None
+    irregular = irregular_sweep(ag, torch, dev, stream, n=args.irregular_n,
+                                stripes=args.irregular_stripes) if "irregular" in args.legs else None
+    clients = batch_clients(ag, torch, dev, stream) if "clients" in args.legs else None
+    serving = serve_sweep(ag, torch, dev) if "serving" in args.legs else None
 
     # end to end through host buffers: H2D of b, c, the three guarded kernels, D2H of a
-    e2e_steps = max(3, min(args.steps // 100, 10))
-    hb = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
-    hc = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
-    ha = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
-    hb.copy_(B.cpu())
-    hc.copy_(C.cpu())
-    with torch.cuda.stream(stream):
-        def e2e_step():
-            B.copy_(hb, non_blocking=True)
-            C.copy_(hc, non_blocking=True)
-            step(True)
-            ha.copy_(A, non_blocking=True)
-        e2e_step()
-        torch.cuda.synchronize()
-        barrier(ws)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1), dev)
-    e2e = {"value": ws * STEP_BYTES * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": 2 * 4 * N_ELEMS, "d2h_bytes_per_step": 4 * N_ELEMS,
-           "steps": e2e_steps}
+    e2e = end_to_end(torch, ws, dev, stream, step, A, B, C, max(3, min(args.steps // 100, 10))) \
+        if "e2e" in args.legs else None
 
     cpu = None
-    if rank == 0:
+    if rank == 0 and "cpu" in args.legs:
         import oracle
         oracle.build()
         n_sample = 1 << 27
@@ -357,9 +339,11 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": WORKLOAD, "elements": N_ELEMS, "table_ranges": len(r),
                        "page_bytes": 1 << 21, "policy": "poison",
                        "l2": "each array 1 GiB, larger than the 126 MB L2; no flush needed"},
-            "unguarded_gbs": value_u, "guarded_over_unguarded": value / ws / value_u,
+            "unguarded_gbs": value_u,
+            "guarded_over_unguarded": value / ws / value_u if value_u else None,
             "ptx_injected_gbs": ptx_gbs, "ptx_plain_gbs": ptx_plain_gbs,
-            "ptx_injected_over_plain": ptx_gbs / ptx_plain_gbs, "ptx_kernel_ms": ptx_kern,
+            "ptx_injected_over_plain": ptx_gbs / ptx_plain_gbs if ptx_gbs else None,
+            "ptx_kernel_ms": ptx_kern,
             "kernel_ms": {f"{op}_guarded": kern[op] for op in ops} |
                          {f"{op}_unguarded": kern_u[op] for op in ops},
             "roofline": roofline, "batch_check": batch, "irregular": irregular, "batch_clients": clients, "serving": serving,
@@ -367,6 +351,38 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": args.steps * 4, "clocks": ck, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
+
+
+def end_to_end(torch, ws, dev, stream, step, A, B, C, steps):
+    """The workload through the public API from pinned host buffers: every step copies b
+    and c in, runs the three guarded kernels and copies a out."""
+    hb = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
+    hc = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
+    ha = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
+    hb.copy_(B.cpu())
+    hc.copy_(C.cpu())
+
+    def one():
+        B.copy_(hb, non_blocking=True)
+        C.copy_(hc, non_blocking=True)
+        step(True)
+        ha.copy_(A, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        one()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1), dev)
+    return {"value": ws * STEP_BYTES * steps / (ms / 1e3) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": 2 * 4 * N_ELEMS, "d2h_bytes_per_step": 4 * N_ELEMS,
+            "steps": steps}
 
 
 def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):
@@ -452,13 +468,13 @@ def batch_clients(ag, torch, dev, stream, n_clients=256, reps=5):
 
 
 
-def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5):
+def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
     """Gather / scatter / histogram over the 16 GiB striped table (4096 user allocations of
     4 MiB, each followed by a 64 KiB protected range), 2^28 int64 indices, uniform and
     Zipf(1.1), 0.1% aimed into protected ranges; guarded (poison, 2 MiB and 64 KiB pages)
     against unguarded. Indices are drawn on the device with a seeded torch generator."""
-    r, span, off = syn.irregular_layout(n)
-    stripes, ue = 4096, (4 << 20) // 4
+    r, span, off = syn.irregular_layout(n, stripes)
+    ue = (4 << 20) // 4
     se, pe, bins = ((4 << 20) + (64 << 10)) // 4, (64 << 10) // 4, 1 << 20
     arena = torch.empty(span, dtype=torch.uint8, device=dev)
     base = arena.data_ptr()
@@ -612,7 +628,14 @@ def main():
     ap.add_argument("--batch-only", type=int, default=0, metavar="N",
                     help="only time the batch check on N accesses (profiling)")
     ap.add_argument("--batch-page", type=int, default=16, help="log2 page size for --batch-only")
+    ap.add_argument("--legs", default="all",
+                    help="comma list of extra legs: unguarded,ptx,batch,irregular,clients,serving,"
+                         "e2e,cpu (the guarded steps always run)")
+    ap.add_argument("--irregular-n", type=int, default=1 << 28)
+    ap.add_argument("--irregular-stripes", type=int, default=4096)
     args = ap.parse_args()
+    args.legs = {"unguarded", "ptx", "batch", "irregular", "clients", "serving", "e2e", "cpu"} \
+        if args.legs == "all" else set(args.legs.split(","))
     global N_ELEMS, STEP_BYTES
     N_ELEMS = args.elements - args.elements % 4
     STEP_BYTES = sum(BYTES_PER_ELEM.values()) * N_ELEMS

@@ -50,7 +50,8 @@ enum {
     AGILE_DENY_MMIO = 2,      /* touches the protected I/O aperture                   */
     AGILE_DENY_STRADDLE = 3,  /* touches user memory but not inside one allocation    */
     AGILE_DENY_UNMAPPED = 4,  /* touches no range: hole, freed or unknown address     */
-    AGILE_DENY_INVALID = 5    /* zero or illegal width, or end beyond 2^64-1          */
+    AGILE_DENY_INVALID = 5,   /* zero or illegal width, or end beyond 2^64-1          */
+    AGILE_DENY_NOT_EXACT = 6  /* DMA registration: inside an allocation, not all of it */
 };
 
 /* Violation policies (Sec. V-E). TRAP exists only as instrumented PTX text. */
@@ -178,6 +179,15 @@ AGILE_API void agile_guard_table_destroy(agile_guard_table_t *t);
 AGILE_API int agile_validate_args(const agile_guard_table_t *t, const uint64_t *h_ptr,
                         const uint64_t *h_bytes, size_t n, uint8_t *h_verdict,
                         uint32_t *h_range_id);
+
+/* DMA-registration check (Sec. V-C: a service-backed module may register a user buffer
+ * for device DMA, but only an exact live user allocation is accepted): for each
+ * (h_ptr[i], h_bytes[i]) ALLOW only when it is exactly one user range (base and size);
+ * AGILE_DENY_NOT_EXACT when it lies strictly inside one; else the verdict of
+ * agile_validate_args. Host only, synchronous; AGILE_VIOLATION if any pair was refused. */
+AGILE_API int agile_validate_dma(const agile_guard_table_t *t, const uint64_t *h_ptr,
+                                 const uint64_t *h_bytes, size_t n, uint8_t *h_verdict,
+                                 uint32_t *h_range_id);
 
 /* ---------------------------------------------------------------- violation log */
 

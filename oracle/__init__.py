@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "agile_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-VERDICT_NAMES = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID"]
+VERDICT_NAMES = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID", "NOT_EXACT"]
 NO_RANGE = 0xFFFFFFFF
 POLICY = {"poison": 0, "sink": 1, "report": 2}
 STREAM_OPS = {"copy": 0, "scale": 1, "triad": 2}
@@ -120,6 +120,20 @@ def validate(r, ptr: np.ndarray, nbytes: np.ndarray):
     rid = np.empty(m, dtype=np.uint32)
     _L().orc_validate(ctypes.c_size_t(len(base)), _p(base), _p(size), _p(kind), _p(ident),
                       ctypes.c_size_t(m), _p(ptr), _p(nbytes), _p(verdict), _p(rid))
+    return verdict, rid
+
+
+def validate_exact(r, ptr: np.ndarray, nbytes: np.ndarray):
+    """DMA registration, Sec. V-C: accepted only for an exact live user allocation;
+    a byte range strictly inside one is NOT_EXACT (6); otherwise the ordinary verdict."""
+    base, size, kind, ident = _table(r)
+    ptr = np.ascontiguousarray(ptr, dtype=np.uint64)
+    nbytes = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    m = len(ptr)
+    verdict = np.empty(m, dtype=np.uint8)
+    rid = np.empty(m, dtype=np.uint32)
+    _L().orc_validate_exact(ctypes.c_size_t(len(base)), _p(base), _p(size), _p(kind), _p(ident),
+                            ctypes.c_size_t(m), _p(ptr), _p(nbytes), _p(verdict), _p(rid))
     return verdict, rid
 
 

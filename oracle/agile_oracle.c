@@ -38,7 +38,8 @@
 #include <string.h>
 
 enum { K_USER = 0, K_PROTECTED = 1, K_MMIO = 2 };
-enum { V_ALLOW = 0, V_PROTECTED = 1, V_MMIO = 2, V_STRADDLE = 3, V_UNMAPPED = 4, V_INVALID = 5 };
+enum { V_ALLOW = 0, V_PROTECTED = 1, V_MMIO = 2, V_STRADDLE = 3, V_UNMAPPED = 4, V_INVALID = 5,
+       V_NOT_EXACT = 6 };
 enum { P_POISON = 0, P_SINK = 1, P_REPORT = 2 };
 #define NO_RANGE 0xFFFFFFFFu
 
@@ -222,6 +223,33 @@ void orc_validate(size_t n, const uint64_t *base, const uint64_t *size, const ui
     for (size_t i = 0; i < m; ++i) {
         uint32_t rid;
         verdict[i] = (uint8_t)classify_linear(&t, ptr[i], bytes[i], &rid);
+        if (rid_out) rid_out[i] = rid;
+    }
+}
+
+/* DMA registration (Sec. V-C: a module may register a user buffer for device DMA, "but the
+ * request is accepted only for an exact live user allocation"): allowed only when
+ * (ptr, bytes) is exactly one user range; a byte range strictly inside one is NOT_EXACT;
+ * anything else gets the ordinary verdict. */
+void orc_validate_exact(size_t n, const uint64_t *base, const uint64_t *size, const uint32_t *kind,
+                        const uint32_t *id, size_t m, const uint64_t *ptr, const uint64_t *bytes,
+                        uint8_t *verdict, uint32_t *rid_out) {
+    orc_table t = {n, base, size, kind, id};
+    for (size_t i = 0; i < m; ++i) {
+        uint32_t rid = NO_RANGE, v = V_NOT_EXACT;
+        int exact = 0;
+        for (size_t j = 0; j < n; ++j)
+            if (kind[j] == K_USER && base[j] == ptr[i] && size[j] == bytes[i]) {
+                exact = 1;
+                rid = id[j];
+            }
+        if (exact) {
+            v = V_ALLOW;
+        } else {
+            v = classify_linear(&t, ptr[i], bytes[i], &rid);
+            if (v == V_ALLOW) v = V_NOT_EXACT;
+        }
+        verdict[i] = (uint8_t)v;
         if (rid_out) rid_out[i] = rid;
     }
 }

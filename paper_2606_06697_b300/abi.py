@@ -17,7 +17,7 @@ library_path = os.path.join(_HERE, "libagileguard.so")
 
 LOG_BYTES = 64
 NO_RANGE = 0xFFFFFFFF
-VERDICTS = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID"]
+VERDICTS = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID", "NOT_EXACT"]
 KINDS = {"user": 0, "protected": 1, "mmio": 2}
 POLICIES = {"poison": 0, "sink": 1, "report": 2, "trap": 3}
 OPS = {"copy": 0, "scale": 1, "triad": 2}
@@ -112,6 +112,7 @@ _SIG = {
     "agile_guard_table_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
     "agile_guard_table_destroy": (None, [_P]),
     "agile_validate_args": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P]),
+    "agile_validate_dma": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P]),
     "agile_violation_log_init": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
     "agile_violation_log_read": (ctypes.c_int, [_P, _P, _P]),
     "agile_guard_check_batch": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
@@ -289,6 +290,18 @@ def agile_validate_args(table: Table, ptr, nbytes):
     rc = _check(lib().agile_validate_args(table.handle, ptr.ctypes.data, nbytes.ctypes.data,
                                           len(ptr), v.ctypes.data, rid.ctypes.data),
                 "agile_validate_args", ok=(0, 1))
+    return rc, v, rid
+
+
+def agile_validate_dma(table: Table, ptr, nbytes):
+    """DMA registration check: (rc, verdict uint8[n], range_id uint32[n])."""
+    ptr = _np(ptr, np.uint64)
+    nbytes = _np(nbytes, np.uint64)
+    v = np.empty(len(ptr), np.uint8)
+    rid = np.empty(len(ptr), np.uint32)
+    rc = _check(lib().agile_validate_dma(table.handle, ptr.ctypes.data, nbytes.ctypes.data,
+                                         len(ptr), v.ctypes.data, rid.ctypes.data),
+                "agile_validate_dma", ok=(0, 1))
     return rc, v, rid
 
 

@@ -231,4 +231,25 @@ int agile_validate_args(const agile_guard_table_t *t, const uint64_t *h_ptr,
     return any ? AGILE_VIOLATION : AGILE_OK;
 }
 
+int agile_validate_dma(const agile_guard_table_t *t, const uint64_t *h_ptr,
+                       const uint64_t *h_bytes, size_t n, uint8_t *h_verdict,
+                       uint32_t *h_range_id) {
+    if (t == nullptr || (n > 0 && (h_ptr == nullptr || h_bytes == nullptr || h_verdict == nullptr)))
+        return AGILE_ERR_INVALID_ARG;
+    int any = 0;
+    for (size_t i = 0; i < n; ++i) {
+        uint32_t rid;
+        uint32_t v = agile::classify_host(*t, h_ptr[i], h_bytes[i], &rid);
+        if (v == AGILE_ALLOW) {
+            // the containing allocation is the last range starting at or below ptr
+            const size_t j = std::upper_bound(t->base.begin(), t->base.end(), h_ptr[i]) - t->base.begin() - 1;
+            if (!(t->base[j] == h_ptr[i] && t->end[j] - t->base[j] == h_bytes[i])) v = AGILE_DENY_NOT_EXACT;
+        }
+        h_verdict[i] = (uint8_t)v;
+        if (h_range_id) h_range_id[i] = rid;
+        any |= v != AGILE_ALLOW;
+    }
+    return any ? AGILE_VIOLATION : AGILE_OK;
+}
+
 }  // extern "C"

@@ -149,3 +149,20 @@ int main(void) {
     mirrors = [abi._Range, abi._DevTable, abi._Record, abi.Work, abi.BatchConfig, abi.Request,
                abi.Completion, abi.WorkerConfig]
     assert sizes == [ctypes.sizeof(m) for m in mirrors]
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_validate_dma_matches_oracle(seed):
+    t = syn.batch_table(seed=syn.SEED_BASE + 80 + seed)
+    st = syn.Stream(seed, 81)
+    n = 5000
+    j = st.below(len(t), n)
+    base, size = t.base.astype(np.int64), t.size.astype(np.int64)
+    mode = st.below(4, n)
+    ptr = np.where(mode == 3, base[j] + st.below(size[j], n), base[j])
+    nb = np.where(mode == 0, size[j], np.where(mode == 1, size[j] - 1, st.log_uniform(1, 1 << 20, n)))
+    tbl = ag.agile_guard_table_build(t.base, t.size, t.kind, t.ident, 21)
+    rc, v, rid = ag.agile_validate_dma(tbl, ptr.astype(np.uint64), np.maximum(nb, 0).astype(np.uint64))
+    ov, orid = oracle.validate_exact(t, ptr.astype(np.uint64), np.maximum(nb, 0).astype(np.uint64))
+    assert (v == ov).all() and (rid == orid).all()
+    assert (v == 0).any() and (v == 6).any()

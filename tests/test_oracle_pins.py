@@ -369,3 +369,37 @@ def test_irregular_denied_index_load_reads_zero():
     want[4:12] = tvals[0]
     assert (got == want).all()
     assert log.count == 4 and (log.key, log.site, log.width, log.range_id) == (b0 + 32, 0, 16, 0x99)
+
+
+def test_dma_exact_allocation():
+    """Sec. V-C: DMA registration is accepted only for an exact live user allocation."""
+    t = syn._ranges([0x1000, 0x2000, 0x3000], [0x800, 0x400, 0x100], [0, 0, 1], [1, 2, 3])
+    cases = [  # (ptr, bytes, verdict)
+        (0x1000, 0x800, "ALLOW"), (0x2000, 0x400, "ALLOW"),
+        (0x1000, 0x7FF, "NOT_EXACT"), (0x1001, 0x7FF, "NOT_EXACT"), (0x2100, 0x10, "NOT_EXACT"),
+        (0x1000, 0x801, "STRADDLE"), (0x3000, 0x100, "PROTECTED"), (0x5000, 0x10, "UNMAPPED"),
+        (0x1000, 0, "INVALID"),
+    ]
+    v, rid = oracle.validate_exact(t, np.array([c[0] for c in cases], np.uint64),
+                                   np.array([c[1] for c in cases], np.uint64))
+    assert [oracle.VERDICT_NAMES[x] for x in v] == [c[2] for c in cases]
+    assert rid[:2].tolist() == [1, 2] and rid[2] == 1
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_dma_exact_random_against_membership(seed):
+    """Exact-match membership in the set of user (base, size) pairs decides ALLOW; every
+    other pair carries validate's verdict, with ALLOW turned into NOT_EXACT."""
+    t = syn.batch_table(seed=syn.SEED_BASE + 70 + seed)
+    st = syn.Stream(seed, 71)
+    users = np.flatnonzero(t.kind == 0)
+    n = 3000
+    j = users[st.below(len(users), n)]
+    shrink = st.below(3, n)                       # 0: exact, 1: shorter, 2: later start
+    ptr = t.base[j].astype(np.int64) + np.where(shrink == 2, 256, 0)
+    nb = t.size[j].astype(np.int64) - np.where(shrink > 0, 256, 0)
+    v, _ = oracle.validate_exact(t, ptr.astype(np.uint64), nb.astype(np.uint64))
+    exact = set(zip(t.base[users].tolist(), t.size[users].tolist()))
+    want_allow = np.array([(int(p), int(b)) in exact for p, b in zip(ptr, nb)])
+    assert ((v == 0) == want_allow).all()
+    assert (v[~want_allow] == 6).all()            # all are inside an allocation
