@@ -388,6 +388,53 @@ def irregular_indices(n: int, stripes: int = 4096, user_bytes: int = 4 * MiB,
     return idx, key, bad
 
 
+def remap_layout(n_idx: int, half: int = MiB):
+    """Arena layout for the REMAP_OR policy with mask `half` (a power of two); the arena
+    start must be aligned to 2 * half. Block [0, 2 half): a protected shadow in the lower
+    half under the user table T in the upper half, so an access into the shadow ORed with
+    the mask lands in T. Then a protected range at 2 half whose ORed image, 3 half on, is a
+    hole; a second shadow/user pair at [4 half, 6 half) holding the bins (half / 4 u32);
+    the int64 index array and the fp32 output array.
+
+    Returns (ranges_relative, arena_bytes, offsets {'t', 'bins', 'idx', 'out'}).
+    """
+    assert half & (half - 1) == 0 and half >= 64 * KiB
+    base = [0, half, 2 * half, 4 * half, 5 * half]
+    size = [half, half, 64 * KiB, half, half]
+    kind = [KIND_PROTECTED, KIND_USER, KIND_PROTECTED, KIND_PROTECTED, KIND_USER]
+    ident = [0x40, 0x41, 0x42, 0x43, 0x10]
+    off = {"t": half, "bins": 5 * half, "idx": 6 * half + 64 * KiB}
+    base.append(off["idx"]); size.append(8 * n_idx); kind.append(KIND_USER); ident.append(0x12)
+    off["out"] = _round_up(off["idx"] + 8 * n_idx + 64 * KiB, 256)
+    base.append(off["out"]); size.append(4 * n_idx); kind.append(KIND_USER); ident.append(0x13)
+    span = _round_up(off["out"] + 4 * n_idx + 64 * KiB, 2 * half)
+    return _ranges(base, size, kind, ident, half=half), span, off
+
+
+def remap_indices(n: int, half: int = MiB, frac_bad: float = 0.02, seed: int = SEED_BASE + 6):
+    """Element offsets for remap_layout: uniform over T (and over the bins for the keys).
+    int(n * frac_bad) positions are aimed off the buffer: alternately into the shadow below
+    it (negative offsets; class 1) and into the protected range at 2 half (class 2).
+    Returns (idx, key, cls) with cls 0 for an in-buffer access."""
+    st = Stream(seed, 10)
+    ne = half // 4
+    idx = st.below(ne, n).astype(np.int64)
+    key = st.below(ne, n).astype(np.int64)
+    cls = np.zeros(n, dtype=np.int8)
+    nbad = int(n * frac_bad)
+    if nbad:
+        pos = np.unique(st.below(n, nbad))
+        c = np.where(np.arange(len(pos)) % 2 == 0, 1, 2).astype(np.int8)
+        cls[pos] = c
+        j = st.below(16 * KiB, len(pos)).astype(np.int64)
+        sh = -1 - st.below(ne, len(pos)).astype(np.int64)
+        # T starts at half: the shadow is [-ne, 0), the range at 2 half is ne + j;
+        # the bins start at 5 half: the shadow is [-ne, 0), the range at 2 half is -3 ne + j
+        idx[pos] = np.where(c == 1, sh, ne + j)
+        key[pos] = np.where(c == 1, sh, -3 * ne + j)
+    return idx, key, cls
+
+
 # ---------------------------------------------------------------- many clients
 
 def lognormal(stream: Stream, median: float, sigma: float, n: int) -> np.ndarray:

@@ -59,7 +59,10 @@ enum {
     AGILE_POLICY_POISON = 0,  /* denied loads read 0, denied stores/atomics dropped; logged   */
     AGILE_POLICY_SINK = 1,    /* denied loads read a zero page, stores go to a sink; logged   */
     AGILE_POLICY_REPORT = 2,  /* access proceeds unchanged; logged (audit only, not isolating) */
-    AGILE_POLICY_TRAP = 3     /* emit `trap;` before the access (instrumentation only)        */
+    AGILE_POLICY_TRAP = 3,    /* emit `trap;` before the access (instrumentation only)        */
+    AGILE_POLICY_REMAP_OR = 4 /* a denied address is rewritten as addr | remap_or (the table's
+                                 mask, e.g. into Table I's user aperture); the access proceeds
+                                 there only if that address is allowed, else as POISON; logged */
 };
 
 /* Return codes. */
@@ -119,7 +122,7 @@ typedef struct {
     const uint32_t *crange;   /* windows under 4 GiB: n records of 4 u32 {start - lo,
                                  last byte - lo, rank (0 MMIO, 1 protected, 2 user), id};
                                  else NULL                                              */
-    const void *reserved2;
+    uint64_t remap_or;        /* mask the REMAP_OR policy ORs into a denied address     */
 } agile_dev_table_t;
 
 /* Decoded violation log. The first fault is the violating access with the smallest
@@ -152,6 +155,11 @@ typedef struct {
  * array is copied; *out is freed with agile_guard_table_destroy. */
 AGILE_API int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t log2_page,
                             agile_guard_table_t **out);
+
+/* Mask for the REMAP_OR policy (Sec. V-E: "rewrite protected addresses into the user
+ * range"), used by uploads that follow; a multiple of 16 (ALIGN otherwise) so remapped
+ * vector accesses stay aligned. 0 (the default) remaps nothing. */
+AGILE_API int agile_guard_table_set_remap(agile_guard_table_t *t, uint64_t remap_or);
 
 /* Device bytes needed by agile_guard_table_upload for this table. */
 AGILE_API int agile_guard_table_device_bytes(const agile_guard_table_t *t, size_t *bytes);
@@ -239,8 +247,9 @@ enum { AGILE_IRR_GATHER = 0, AGILE_IRR_SCATTER = 1, AGILE_IRR_HIST = 2 };
  * Access order per group of four elements: two 16-byte index loads (sites 0, 1), the
  * four element accesses (site 2), gather's 16-byte output store (site 3); elements past
  * the last whole group use an 8-byte index load, the element access and a 4-byte store.
- * Policies and tbl == NULL as for agile_stream_launch; under POISON a denied index load
- * reads 0 and a denied element load reads 0.0f. */
+ * Policies and tbl == NULL as for agile_stream_launch, plus REMAP_OR (the table's
+ * remap_or mask); under POISON a denied index load reads 0 and a denied element load
+ * reads 0.0f. */
 AGILE_API int agile_irregular_launch(int kind, const agile_dev_table_t *tbl, const int64_t *d_idx,
                                      void *d_base, float *d_out, size_t n, int policy,
                                      void *d_log, void *stream);

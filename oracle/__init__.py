@@ -22,7 +22,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 VERDICT_NAMES = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID", "NOT_EXACT"]
 NO_RANGE = 0xFFFFFFFF
-POLICY = {"poison": 0, "sink": 1, "report": 2}
+POLICY = {"poison": 0, "sink": 1, "report": 2, "remap": 4}
 STREAM_OPS = {"copy": 0, "scale": 1, "triad": 2}
 
 
@@ -170,10 +170,11 @@ IRREGULAR = {"gather": 0, "scatter": 1, "hist": 2}
 
 
 def irregular(kind: str, r, arena: np.ndarray, arena_va: int, va: dict, n: int,
-              policy: str = "poison"):
+              policy: str = "poison", remap: int = 0):
     """Guarded gather / scatter / histogram over an arena copy (Sec. V-E guard and
     policies; access order stated in agile_oracle.c). `arena` (uint8) is updated in
-    place; va: {'idx', 't', 'out'} guarded-space addresses. Returns the Log."""
+    place; va: {'idx', 't', 'out'} guarded-space addresses; remap is the REMAP_OR mask.
+    Returns the Log."""
     base, size, kind_, ident = _table(r)
     assert arena.dtype == np.uint8 and arena.flags.c_contiguous
     log = _Log()
@@ -182,8 +183,8 @@ def irregular(kind: str, r, arena: np.ndarray, arena_va: int, va: dict, n: int,
     rc = f(ctypes.c_int(IRREGULAR[kind]), ctypes.c_size_t(n), ctypes.c_uint64(arena_va),
            _p(arena), ctypes.c_size_t(len(arena)), ctypes.c_uint64(va["idx"]),
            ctypes.c_uint64(va["t"]), ctypes.c_uint64(va.get("out", 0)),
-           ctypes.c_int(POLICY[policy]), ctypes.c_size_t(len(base)), _p(base), _p(size),
-           _p(kind_), _p(ident), ctypes.byref(log))
+           ctypes.c_int(POLICY[policy]), ctypes.c_uint64(remap), ctypes.c_size_t(len(base)),
+           _p(base), _p(size), _p(kind_), _p(ident), ctypes.byref(log))
     if rc != 0:
         raise ValueError("an access that is carried out falls outside the arena")
     return Log._of(log)

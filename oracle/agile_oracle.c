@@ -40,7 +40,7 @@
 enum { K_USER = 0, K_PROTECTED = 1, K_MMIO = 2 };
 enum { V_ALLOW = 0, V_PROTECTED = 1, V_MMIO = 2, V_STRADDLE = 3, V_UNMAPPED = 4, V_INVALID = 5,
        V_NOT_EXACT = 6 };
-enum { P_POISON = 0, P_SINK = 1, P_REPORT = 2 };
+enum { P_POISON = 0, P_SINK = 1, P_REPORT = 2, P_REMAP = 4 };
 #define NO_RANGE 0xFFFFFFFFu
 
 typedef struct {
@@ -331,18 +331,27 @@ static int in_arena(const orc_arena *A, uint64_t a, uint64_t w) {
     return a >= A->va && w <= A->len && a - A->va <= A->len - w;
 }
 
-/* One guarded access: classify, log a deny, and tell whether it is carried out. */
-static int guarded(const orc_sorted *s, orc_log *log, int policy, uint64_t a, uint64_t w,
-                   uint32_t site) {
+/* One guarded access: classify, log a deny, and tell whether it is carried out and at
+ * which address. REMAP (Sec. V-E remap_or, with the paper's caveat that the target must
+ * itself be a live user allocation): a denied access moves to a | remap when that access is
+ * allowed, else it is dropped as under poison. */
+static int guarded(const orc_sorted *s, orc_log *log, int policy, uint64_t remap, uint64_t a,
+                   uint64_t w, uint32_t site, uint64_t *at) {
     uint32_t rid, v = classify_sorted(s, a, w, &rid);
+    *at = a;
     if (v == V_ALLOW) return 1;
     log_note(log, a, a, (uint32_t)w, v, site, rid);
-    return policy == P_REPORT;
+    if (policy == P_REPORT) return 1;
+    if (policy == P_REMAP) {
+        uint32_t r2;
+        if (classify_sorted(s, a | remap, w, &r2) == V_ALLOW) { *at = a | remap; return 1; }
+    }
+    return 0;
 }
 
 int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t arena_len,
-                  uint64_t va_idx, uint64_t va_t, uint64_t va_out, int policy, size_t tn,
-                  const uint64_t *base, const uint64_t *size, const uint32_t *kindv,
+                  uint64_t va_idx, uint64_t va_t, uint64_t va_out, int policy, uint64_t remap,
+                  size_t tn, const uint64_t *base, const uint64_t *size, const uint32_t *kindv,
                   const uint32_t *id, orc_log *log) {
     orc_table t = {tn, base, size, kindv, id};
     orc_sorted *s = sorted_new(&t);
@@ -356,19 +365,19 @@ int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t 
         int64_t idx[4] = {0, 0, 0, 0};
         /* index loads */
         for (size_t h = 0; h < (vec ? 2u : 1u); ++h) {
-            uint64_t a = va_idx + 8 * e0 + 16 * h, w = vec ? 16 : 8;
-            if (guarded(s, log, policy, a, w, (uint32_t)h)) {
-                if (!in_arena(&A, a, w)) { rc = -1; break; }
-                memcpy(idx + 2 * h, arena + (a - A.va), w);
+            uint64_t a = va_idx + 8 * e0 + 16 * h, w = vec ? 16 : 8, at;
+            if (guarded(s, log, policy, remap, a, w, (uint32_t)h, &at)) {
+                if (!in_arena(&A, at, w)) { rc = -1; break; }
+                memcpy(idx + 2 * h, arena + (at - A.va), w);
             }
         }
         /* element accesses */
         float out[4] = {0, 0, 0, 0};
         for (size_t k = 0; k < cnt && rc == 0; ++k) {
-            uint64_t a = va_t + 4 * (uint64_t)idx[k];
-            if (!guarded(s, log, policy, a, 4, 2)) continue;
-            if (!in_arena(&A, a, 4)) { rc = -1; break; }
-            uint8_t *p = arena + (a - A.va);
+            uint64_t a = va_t + 4 * (uint64_t)idx[k], at;
+            if (!guarded(s, log, policy, remap, a, 4, 2, &at)) continue;
+            if (!in_arena(&A, at, 4)) { rc = -1; break; }
+            uint8_t *p = arena + (at - A.va);
             if (kind == IR_GATHER) {
                 memcpy(&out[k], p, 4);
             } else if (kind == IR_SCATTER) {
@@ -383,10 +392,10 @@ int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t 
         }
         /* gather's output store */
         if (kind == IR_GATHER && rc == 0) {
-            uint64_t a = va_out + 4 * e0, w = 4 * cnt;
-            if (guarded(s, log, policy, a, w, 3)) {
-                if (!in_arena(&A, a, w)) rc = -1;
-                else memcpy(arena + (a - A.va), out, w);
+            uint64_t a = va_out + 4 * e0, w = 4 * cnt, at;
+            if (guarded(s, log, policy, remap, a, w, 3, &at)) {
+                if (!in_arena(&A, at, w)) rc = -1;
+                else memcpy(arena + (at - A.va), out, w);
             }
         }
     }

@@ -19,7 +19,7 @@ LOG_BYTES = 64
 NO_RANGE = 0xFFFFFFFF
 VERDICTS = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID", "NOT_EXACT"]
 KINDS = {"user": 0, "protected": 1, "mmio": 2}
-POLICIES = {"poison": 0, "sink": 1, "report": 2, "trap": 3}
+POLICIES = {"poison": 0, "sink": 1, "report": 2, "trap": 3, "remap": 4}
 OPS = {"copy": 0, "scale": 1, "triad": 2}
 IRREGULAR = {"gather": 0, "scatter": 1, "hist": 2}
 WORK = {"copy": 0, "scale": 1, "triad": 2, "gather": 3, "scatter": 4, "hist": 5}
@@ -44,7 +44,7 @@ class _DevTable(ctypes.Structure):
                 ("zero_page", ctypes.c_void_p), ("sink_page", ctypes.c_void_p),
                 ("bytes", ctypes.c_uint64), ("search_steps", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("crange", ctypes.c_void_p),
-                ("reserved2", ctypes.c_void_p)]
+                ("remap_or", ctypes.c_uint64)]
 
 
 class _Record(ctypes.Structure):
@@ -108,6 +108,7 @@ _P = ctypes.c_void_p
 _SIG = {
     "agile_guard_table_build": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, _P]),
     "agile_guard_table_device_bytes": (ctypes.c_int, [_P, _P]),
+    "agile_guard_table_set_remap": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "agile_guard_table_geometry": (ctypes.c_int, [_P, _P, _P]),
     "agile_guard_table_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
     "agile_guard_table_destroy": (None, [_P]),
@@ -253,6 +254,10 @@ class Table:
         _check(lib().agile_guard_table_geometry(self._h, ctypes.byref(lg), ctypes.byref(npg)),
                "agile_guard_table_geometry")
         return lg.value, npg.value
+
+    def set_remap(self, mask: int) -> None:
+        """agile_guard_table_set_remap: the REMAP_OR mask for later uploads."""
+        _check(lib().agile_guard_table_set_remap(self._h, mask), "agile_guard_table_set_remap")
 
     def upload(self, buf, stream=None) -> DevTable:
         """agile_guard_table_upload into `buf` (a uint8 CUDA tensor of >= device_bytes)."""

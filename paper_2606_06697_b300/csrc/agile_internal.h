@@ -17,6 +17,7 @@ struct agile_guard_table {
     std::vector<uint32_t> kind, id;
     std::vector<uint32_t> page;           // npages + 1 entries
     uint32_t search_steps = 0;            // steps covering the largest page slice
+    uint64_t remap_or = 0;                // REMAP_OR policy mask
     std::vector<unsigned char> staging;   // host image of the device buffer
     size_t off_base = 0, off_end = 0, off_kind = 0, off_id = 0, total = 0;
     bool compact = false;                 // window < 4 GiB: packed 32-bit records exist

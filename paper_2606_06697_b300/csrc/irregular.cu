@@ -70,6 +70,7 @@ int dispatch(const agile_dev_table_t *tbl, const int64_t *idx, void *base, float
         case AGILE_POLICY_POISON: return by_mode<KIND, AGILE_POLICY_POISON>(*tbl, idx, base, out, n, log, st);
         case AGILE_POLICY_SINK: return by_mode<KIND, AGILE_POLICY_SINK>(*tbl, idx, base, out, n, log, st);
         case AGILE_POLICY_REPORT: return by_mode<KIND, AGILE_POLICY_REPORT>(*tbl, idx, base, out, n, log, st);
+        case AGILE_POLICY_REMAP_OR: return by_mode<KIND, AGILE_POLICY_REMAP_OR>(*tbl, idx, base, out, n, log, st);
         default: return AGILE_ERR_INVALID_ARG;
     }
 }
@@ -80,7 +81,8 @@ extern "C" int agile_irregular_launch(int kind, const agile_dev_table_t *tbl, co
                                       void *d_base, float *d_out, size_t n, int policy,
                                       void *d_log, void *stream) {
     if (kind < AGILE_IRR_GATHER || kind > AGILE_IRR_HIST) return AGILE_ERR_INVALID_ARG;
-    if (policy < AGILE_POLICY_POISON || policy > AGILE_POLICY_REPORT) return AGILE_ERR_INVALID_ARG;
+    if (policy < AGILE_POLICY_POISON || policy > AGILE_POLICY_REMAP_OR || policy == AGILE_POLICY_TRAP)
+        return AGILE_ERR_INVALID_ARG;
     if (n == 0) return AGILE_OK;
     if (d_idx == nullptr || d_base == nullptr || (kind == AGILE_IRR_GATHER && d_out == nullptr))
         return AGILE_ERR_INVALID_ARG;

@@ -25,9 +25,32 @@ __device__ __forceinline__ bool lane_check(const TView &V, uint64_t a, uint32_t 
     return false;
 }
 
+// REMAP_OR (Sec. V-E remap_or, made safe as the paper asks): a denied access moves to its
+// address with the table's mask ORed in, if that access is allowed. Returns the address to
+// use for a denied access under POLICY, or 0 for "drop it / read the zero page".
+template <int POLICY>
+__device__ __forceinline__ uint64_t remapped(const TView &V, const agile_dev_table_t &T,
+                                             uint64_t a, uint32_t w) {
+    if constexpr (POLICY != AGILE_POLICY_REMAP_OR) {
+        return 0ull;
+    } else {
+        const uint64_t a2 = a | T.remap_or;
+        uint32_t rid;
+        return classify(V, a2, w, &rid) == AGILE_ALLOW ? a2 : 0ull;
+    }
+}
+
 template <int KIND, int POLICY>
-__device__ __forceinline__ float element(float *addr, bool ok, int64_t e, const agile_dev_table_t &T) {
+__device__ __forceinline__ float element(const TView &V, float *addr, bool ok, int64_t e,
+                                         const agile_dev_table_t &T) {
     constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
+    if constexpr (POLICY == AGILE_POLICY_REMAP_OR) {
+        if (!ok) {
+            const uint64_t a2 = remapped<POLICY>(V, T, (uint64_t)addr, 4);
+            ok = a2 != 0;
+            if (ok) addr = reinterpret_cast<float *>(a2);
+        }
+    }
     if constexpr (KIND == AGILE_IRR_GATHER) {
         return __ldg((ok || kAlways) ? addr : reinterpret_cast<const float *>(T.zero_page));
     } else if constexpr (KIND == AGILE_IRR_SCATTER) {
@@ -41,6 +64,15 @@ __device__ __forceinline__ float element(float *addr, bool ok, int64_t e, const 
             atomicAdd(reinterpret_cast<unsigned int *>(T.sink_page), 1u);
         return 0.f;
     }
+}
+
+// Source of a guarded load: the access itself, its remapped address, or the zero page.
+template <int POLICY, typename P>
+__device__ __forceinline__ const P *load_src(const TView &V, const agile_dev_table_t &T,
+                                             const P *p, bool ok, uint32_t w) {
+    if (ok || POLICY == AGILE_POLICY_REPORT) return p;
+    const uint64_t a2 = remapped<POLICY>(V, T, (uint64_t)p, w);
+    return a2 ? reinterpret_cast<const P *>(a2) : reinterpret_cast<const P *>(T.zero_page);
 }
 
 // Units u0 .. u0+31 (one per lane, clipped to n4). Warp-collective only in its uniform
@@ -70,20 +102,27 @@ __device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_
         }
     }
     if (!act) return;
-    const longlong2 p0 = __ldg((ok0 || kAlways) ? idx2 + 2 * u : zero2);
-    const longlong2 p1 = __ldg((ok1 || kAlways) ? idx2 + 2 * u + 1 : zero2);
+    const longlong2 p0 = __ldg(load_src<POLICY>(V, T, idx2 + 2 * u, ok0, 16));
+    const longlong2 p1 = __ldg(load_src<POLICY>(V, T, idx2 + 2 * u + 1, ok1, 16));
+    (void)zero2;
     const int64_t e[4] = {p0.x, p0.y, p1.x, p1.y};
     float v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float *addr = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e[k]);
         const bool ok = !GUARD || lane_check(V, (uint64_t)addr, 4, 2, ll);
-        v[k] = element<KIND, POLICY>(addr, ok, e[k], T);
+        v[k] = element<KIND, POLICY>(V, addr, ok, e[k], T);
     }
     if constexpr (kGather) {
         const float4 o = make_float4(v[0], v[1], v[2], v[3]);
-        if (oko || kAlways) __stcs(out4 + u, o);
-        else if constexpr (POLICY == AGILE_POLICY_SINK) __stcs(reinterpret_cast<float4 *>(T.sink_page), o);
+        if (oko || kAlways) {
+            __stcs(out4 + u, o);
+        } else if constexpr (POLICY == AGILE_POLICY_SINK) {
+            __stcs(reinterpret_cast<float4 *>(T.sink_page), o);
+        } else if constexpr (POLICY == AGILE_POLICY_REMAP_OR) {
+            const uint64_t a2 = remapped<POLICY>(V, T, (uint64_t)(out4 + u), 16);
+            if (a2) __stcs(reinterpret_cast<float4 *>(a2), o);
+        }
     }
 }
 
@@ -96,14 +135,20 @@ __device__ __forceinline__ void irregular_tail(const TView &V, const agile_dev_t
     const size_t i = (n >> 2) * 4 + (threadIdx.x & 31);
     if (i >= n) return;
     const bool oki = !GUARD || lane_check(V, (uint64_t)(idx + i), 8, 0, ll);
-    const int64_t e = *((oki || kAlways) ? idx + i : reinterpret_cast<const int64_t *>(T.zero_page));
+    const int64_t e = *load_src<POLICY>(V, T, idx + i, oki, 8);
     float *addr = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e);
     const bool ok = !GUARD || lane_check(V, (uint64_t)addr, 4, 2, ll);
-    const float v = element<KIND, POLICY>(addr, ok, e, T);
+    const float v = element<KIND, POLICY>(V, addr, ok, e, T);
     if constexpr (KIND == AGILE_IRR_GATHER) {
         const bool oko = !GUARD || lane_check(V, (uint64_t)(out + i), 4, 3, ll);
-        if (oko || kAlways) out[i] = v;
-        else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = v;
+        if (oko || kAlways) {
+            out[i] = v;
+        } else if constexpr (POLICY == AGILE_POLICY_SINK) {
+            *reinterpret_cast<float *>(T.sink_page) = v;
+        } else if constexpr (POLICY == AGILE_POLICY_REMAP_OR) {
+            const uint64_t a2 = remapped<POLICY>(V, T, (uint64_t)(out + i), 4);
+            if (a2) *reinterpret_cast<float *>(a2) = v;
+        }
     }
 }
 

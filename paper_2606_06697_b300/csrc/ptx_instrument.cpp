@@ -242,7 +242,7 @@ class Rewriter {
     }
 
     std::string prologue() const {
-        return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<6>;\n"
+        return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<8>;\n"
                "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
                "\tld.global.u64 %__agT7, [__agile_guard_table];\n"
                "\tld.global.u64 %__agT0, [%__agT7];\n"
@@ -416,6 +416,43 @@ class Rewriter {
             }
         } else if (policy_ == AGILE_POLICY_TRAP) {
             g += "\t@!%__agp3 trap;\n";
+        } else if (policy_ == AGILE_POLICY_REMAP_OR) {
+            // A denied access moves to addr | remap_or (header offset 104) when that access
+            // is allowed (checked without logging); otherwise it is dropped as under poison.
+            const std::string R = "$__AG_RM_" + std::to_string(label_++);
+            const std::string W = std::to_string(acc.width);
+            g += "\tmov.b64 %__agd5, %__agd0;\n"
+                 "\tmov.pred %__agp4, %__agp3;\n"
+                 "\t@%__agp3 bra " + R + ";\n"
+                 "\tld.global.u64 %__agd6, [%__agT7+104];\n"
+                 "\tor.b64 %__agd6, %__agd0, %__agd6;\n"
+                 "\t{\n"
+                 "\t.param .b64 __aga;\n\t.param .b32 __agw;\n\t.param .b32 __ags;\n"
+                 "\t.param .b32 __agl;\n\t.param .b32 __agret;\n"
+                 "\tst.param.b64 [__aga], %__agd6;\n"
+                 "\tst.param.b32 [__agw], " + W + ";\n"
+                 "\tst.param.b32 [__ags], 0;\n"
+                 "\tst.param.b32 [__agl], 0;\n"
+                 "\tcall (__agret), __agile_guard_check, (__aga, __agw, __ags, __agl);\n"
+                 "\tld.param.b32 %__agr2, [__agret];\n"
+                 "\t}\n"
+                 "\tsetp.ne.u32 %__agp4, %__agr2, 0;\n"
+                 "\tmov.b64 %__agd5, %__agd6;\n" + R + ":\n";
+            if (!writes) {
+                g += "\tselp.b64 %__agd5, %__agd5, %__agT3, %__agp4;\n";   // else the zero page
+            } else {
+                // a dropped atomic returns 0 (decided before the original predicate joins in,
+                // so an access predicated off keeps its destination)
+                if (acc.dest_bits)
+                    g += "\t@!%__agp4 mov.b" + std::to_string(acc.dest_bits) + " " + acc.dest + ", 0;\n";
+                if (!pred.empty()) {
+                    if (!neg) g += "\tand.pred %__agp4, %__agp4, " + pred + ";\n";
+                    else g += "\tnot.pred %__agp2, " + pred + ";\n\tand.pred %__agp4, %__agp4, %__agp2;\n";
+                }
+                new_pred = true;
+            }
+            instr = instr.substr(0, ilb) + "[%__agd5]" + instr.substr(irb + 1);
+            if (new_pred) instr = "@%__agp4 " + instr.substr(op_start - start);
         }
         g += "\t" + instr;
         return g;
@@ -472,11 +509,13 @@ class Rewriter {
         g += "\tmov.u32 %__agr2, 1;\n"
              "\t@%__agp1 bra " + L + ";\n"
              "\t{\n"
-             "\t.param .b64 __aga;\n\t.param .b32 __agw;\n\t.param .b32 __ags;\n\t.param .b32 __agret;\n"
+             "\t.param .b64 __aga;\n\t.param .b32 __agw;\n\t.param .b32 __ags;\n"
+             "\t.param .b32 __agl;\n\t.param .b32 __agret;\n"
              "\tst.param.b64 [__aga], %__agd0;\n"
              "\tst.param.b32 [__agw], " + W + ";\n"
              "\tst.param.b32 [__ags], " + std::to_string(site) + ";\n"
-             "\tcall (__agret), __agile_guard_check, (__aga, __agw, __ags);\n"
+             "\tst.param.b32 [__agl], 1;\n"
+             "\tcall (__agret), __agile_guard_check, (__aga, __agw, __ags, __agl);\n"
              "\tld.param.b32 %__agr2, [__agret];\n"
              "\t}\n" + L + ":\n"
              "\tsetp.ne.u32 %__agp3, %__agr2, 0;\n";
@@ -492,7 +531,7 @@ extern "C" int agile_guard_instrument_ptx(const char *ptx, size_t len,
     *out = nullptr;
     *out_len = 0;
     int policy = opts ? opts->policy : AGILE_POLICY_POISON;
-    if (policy < AGILE_POLICY_POISON || policy > AGILE_POLICY_TRAP) return AGILE_ERR_INVALID_ARG;
+    if (policy < AGILE_POLICY_POISON || policy > AGILE_POLICY_REMAP_OR) return AGILE_ERR_INVALID_ARG;
     std::set<std::string> skip;
     if (opts && opts->nskip) {
         if (opts->skip == nullptr) return AGILE_ERR_INVALID_ARG;

@@ -168,6 +168,13 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
     return AGILE_OK;
 }
 
+int agile_guard_table_set_remap(agile_guard_table_t *t, uint64_t remap_or) {
+    if (t == nullptr) return AGILE_ERR_INVALID_ARG;
+    if (remap_or & 15) return AGILE_ERR_ALIGN;
+    t->remap_or = remap_or;
+    return AGILE_OK;
+}
+
 int agile_guard_table_device_bytes(const agile_guard_table_t *t, size_t *bytes) {
     if (t == nullptr || bytes == nullptr) return AGILE_ERR_INVALID_ARG;
     *bytes = t->total;
@@ -203,6 +210,7 @@ int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, 
     h.sink_page = d + kSinkOff;
     h.bytes = t->total;
     h.search_steps = t->search_steps;
+    h.remap_or = t->remap_or;
     if (t->compact) h.crange = (const uint32_t *)(d + t->off_crange);
     static_assert(sizeof(agile_dev_table_t) <= kHeaderBytes, "header fits");
     std::memcpy(t->staging.data(), &h, sizeof h);

@@ -113,3 +113,74 @@ def test_irregular_full_size_gather_uniform():
         first = base + 4 * int(idx[bad].min())
         assert (rec.key, rec.addr, rec.site, rec.width, rec.verdict) == (first, first, 2, 4, 1)
         del g
+
+
+# ---------------------------------------------------------------- REMAP_OR
+
+
+def remap_setup(n, half=1 << 20, seed=6):
+    """remap_layout in a device arena aligned to 2 * half (the mask's block)."""
+    r, span, off = syn.remap_layout(n, half)
+    idx, key, cls = syn.remap_indices(n, half, seed=syn.SEED_BASE + seed)
+    host = np.zeros(span, np.uint8)
+    host[:2 * half] = syn.Stream(6, 7).uniform(half // 2).astype(np.float32).view(np.uint8)
+    raw = torch.empty(span + 2 * half, dtype=torch.uint8, device=DEV)
+    skew = (-raw.data_ptr()) % (2 * half)
+    arena = raw[skew:skew + span]
+    return r, off, idx, key, cls, host, arena, arena.data_ptr()
+
+
+def remap_table(r, base, half, log2_page):
+    s = r.shifted(base)
+    t = ag.agile_guard_table_build(s.base, s.size, s.kind, s.ident, log2_page)
+    t.set_remap(half)
+    buf = torch.empty(t.device_bytes(), dtype=torch.uint8, device=DEV)
+    return t, t.upload(buf)
+
+
+@pytest.mark.parametrize("kind", ["gather", "scatter", "hist"])
+@pytest.mark.parametrize("log2_page", [12, 21])
+@pytest.mark.parametrize("n", [5, 40_003])
+def test_irregular_remap_parity(kind, log2_page, n):
+    half = 1 << 20
+    r, off, idx, key, cls, host, arena, base = remap_setup(n, half)
+    put(host, off["idx"], key if kind == "hist" else idx)
+    _, dev = remap_table(r, base, half, log2_page)
+    arena.copy_(torch.from_numpy(host))
+    log = new_log(client=7)
+    target = off["bins"] if kind == "hist" else off["t"]
+    ag.agile_irregular_launch(kind, dev, base + off["idx"], base + target,
+                              base + off["out"], n, "remap", log)
+    rc, rec = ag.agile_violation_log_read(log)
+    va = {"t": base + target, "idx": base + off["idx"], "out": base + off["out"]}
+    olog = oracle.irregular(kind, r.shifted(base), host, base, va, n, "remap", remap=half)
+    assert_remap_arena(kind, arena.cpu().numpy(), host, off, idx, cls, half)
+    assert_log_equal(rec, olog, client=7)
+
+
+def assert_remap_arena(kind, got, want, off, idx, cls, half):
+    """Arena vs the oracle's. A scatter element that a remapped access and a direct one
+    both write gets either value (the kernels run in parallel; the oracle in index order),
+    so those elements are checked against the two candidates and the rest bit for bit."""
+    if kind != "scatter":
+        assert (got == want).all(), kind
+        return
+    ne = half // 4
+    both = np.intersect1d(idx[cls == 1] + ne, idx[cls == 0])
+    t = got[off["t"]:off["t"] + 4 * ne].view(np.float32)
+    direct = (both & 0xFFFFFF).astype(np.float32)
+    moved = ((both - ne).astype(np.uint64) & np.uint64(0xFFFFFF)).astype(np.float32)
+    assert ((t[both] == direct) | (t[both] == moved)).all()
+    got = got.copy()
+    got[off["t"]:off["t"] + 4 * ne].view(np.float32)[both] = \
+        want[off["t"]:off["t"] + 4 * ne].view(np.float32)[both]
+    assert (got == want).all(), kind
+
+
+def test_remap_policy_refused_where_unsupported():
+    """The streaming kernels and batched work items take poison, sink and report only."""
+    r, off, idx, key, cls, host, arena, base = remap_setup(64)
+    _, dev = remap_table(r, base, 1 << 20, 21)
+    x = arena[off["out"]:off["out"] + 256].view(torch.float32)
+    with pytest.raises(ag.AgileError):
+        ag.agile_stream_launch("copy", dev, x, x, None, 64, 1.0, "remap")

@@ -130,3 +130,34 @@ def test_ptx_irregular_parity(policy, n):
                 assert IRR_SITES[kind][rec.site] == olog.site
     finally:
         mod.unload()
+
+
+@pytest.mark.parametrize("n", [7, 40_003])
+def test_ptx_irregular_remap_parity(n):
+    """The pass's REMAP_OR policy on the irregular PTX kernels vs the oracle."""
+    from test_gpu_irregular import assert_remap_arena, put, remap_setup, remap_table
+    half = 1 << 20
+    mod = ag.agile_module_load(ag.agile_guard_instrument_ptx(IRREGULAR, "remap")[0])
+    try:
+        for kind in ("gather", "scatter", "hist"):
+            r, off, idx, key, cls, host, arena, base = remap_setup(n, half)
+            put(host, off["idx"], key if kind == "hist" else idx)
+            _, dev = remap_table(r, base, half, 16)
+            arena.copy_(torch.from_numpy(host))
+            log = new_log(client=6)
+            ag.agile_module_bind(mod, dev, log)
+            target = off["bins"] if kind == "hist" else off["t"]
+            args = [ctypes.c_uint64(base + off["idx"]), ctypes.c_uint64(base + target),
+                    ctypes.c_uint64(base + off["out"]), ctypes.c_uint64(n)]
+            ag.agile_module_launch(mod, f"agile_ptx_{kind}", 148 * 2, 256, args)
+            rc, rec = ag.agile_violation_log_read(log)
+            va = {"t": base + target, "idx": base + off["idx"], "out": base + off["out"]}
+            olog = oracle.irregular(kind, r.shifted(base), host, base, va, n, "remap", remap=half)
+            assert_remap_arena(kind, arena.cpu().numpy(), host, off, idx, cls, half)
+            assert rec.count == olog.count and rec.client == 6
+            if olog.count:
+                assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
+                    (olog.key, olog.addr, olog.width, olog.verdict, olog.range_id), kind
+                assert IRR_SITES[kind][rec.site] == olog.site
+    finally:
+        mod.unload()

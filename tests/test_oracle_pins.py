@@ -371,6 +371,69 @@ def test_irregular_denied_index_load_reads_zero():
     assert log.count == 4 and (log.key, log.site, log.width, log.range_id) == (b0 + 32, 0, 16, 0x99)
 
 
+def _remap_case(n=4003, half=1 << 20, base=0x7E0000000000):
+    r, span, off = syn.remap_layout(n, half)
+    idx, key, cls = syn.remap_indices(n, half)
+    arena = np.zeros(span, np.uint8)
+    st = syn.Stream(6, 7)
+    arena[:2 * half] = st.uniform(half // 2).astype(np.float32).view(np.uint8)
+    va = {"t": base + off["t"], "idx": base + off["idx"], "out": base + off["out"]}
+    return r.shifted(base), arena, base, va, off, idx, key, cls
+
+
+def test_remap_gather_moves_shadow_accesses_into_the_table():
+    """REMAP_OR (Sec. V-E): a denied access whose address ORed with the mask is an allowed
+    access is carried out there; otherwise it is dropped as under poison. Here the mask is
+    the shadow's size, so T[e] for -half/4 <= e < 0 reads T[e + half/4]; the range at 2 half
+    maps into a hole, so those elements read 0. Every denied access is still logged."""
+    half = 1 << 20
+    t, arena, base, va, off, idx, key, cls = _remap_case(half=half)
+    n = len(idx)
+    _put(arena, off["idx"], idx)
+    tv = arena[half:2 * half].view(np.float32).copy()
+    a = arena.copy()
+    log = oracle.irregular("gather", t, a, base, va, n, "remap", remap=half)
+    got = a[off["out"]:off["out"] + 4 * n].view(np.float32)
+    ne = half // 4
+    want = np.where(cls == 0, tv[np.clip(idx, 0, ne - 1)], np.float32(0))
+    want = np.where(cls == 1, tv[np.clip(idx + ne, 0, ne - 1)], want)
+    assert (cls == 1).sum() > 10 and (cls == 2).sum() > 10
+    assert (got == want).all()
+    assert log.count == int((cls != 0).sum())
+    first = int(va["t"] + 4 * idx[cls != 0].min())
+    assert (log.key, log.site, log.verdict, log.range_id) == (first, 2, 1, 0x40)
+    # a zero mask leaves every denied access denied: remap equals poison
+    a0, a1 = arena.copy(), arena.copy()
+    l0 = oracle.irregular("gather", t, a0, base, va, n, "remap", remap=0)
+    l1 = oracle.irregular("gather", t, a1, base, va, n, "poison")
+    assert (a0 == a1).all() and l0 == l1
+
+
+def test_remap_scatter_and_hist():
+    half = 1 << 20
+    t, arena, base, va, off, idx, key, cls = _remap_case(half=half)
+    n, ne = len(idx), half // 4
+    _put(arena, off["idx"], idx)
+    a = arena.copy()
+    log = oracle.irregular("scatter", t, a, base, va, n, "remap", remap=half)
+    T = arena[half:2 * half].view(np.float32).copy()
+    for e, c in zip(idx, cls):                       # in order: later writes win
+        if c == 0:
+            T[e] = np.float32(e & 0xFFFFFF)
+        elif c == 1:
+            T[e + ne] = np.float32(e & 0xFFFFFF)
+    assert (a[half:2 * half].view(np.float32) == T).all()
+    assert (a[:half] == arena[:half]).all()          # the shadow is never written
+    assert log.count == int((cls != 0).sum())
+    va_h = {"t": base + off["bins"], "idx": va["idx"]}
+    a = arena.copy()
+    _put(a, off["idx"], key)
+    log = oracle.irregular("hist", t, a, base, va_h, n, "remap", remap=half)
+    bins = a[off["bins"]:off["bins"] + half].view(np.uint32)
+    want = np.bincount(key[cls == 0], minlength=ne) + np.bincount(key[cls == 1] + ne, minlength=ne)
+    assert (bins == want).all() and log.count == int((cls != 0).sum())
+
+
 def test_dma_exact_allocation():
     """Sec. V-C: DMA registration is accepted only for an exact live user allocation."""
     t = syn._ranges([0x1000, 0x2000, 0x3000], [0x800, 0x400, 0x100], [0, 0, 1], [1, 2, 3])

@@ -37,7 +37,7 @@ def sites(text):
     return re.findall(r"// agile guard: site (\d+), (\S+), (\d+) bytes", text)
 
 
-@pytest.mark.parametrize("policy", ["poison", "sink", "report", "trap"])
+@pytest.mark.parametrize("policy", ["poison", "sink", "report", "trap", "remap"])
 def test_stream_kernels_every_access_guarded(policy):
     out, rep = ag.agile_guard_instrument_ptx(STREAM, policy)
     n_acc = len(re.findall(r"\b(?:ld|st)\.global\.", STREAM))
@@ -47,7 +47,8 @@ def test_stream_kernels_every_access_guarded(policy):
     assert [x[1] for x in s[:6]] == ["ld.global.v4.f32", "ld.global.v4.f32", "st.global.v4.f32",
                                      "st.global.v4.f32", "ld.global.v4.f32", "st.global.v4.f32"]
     assert [int(x[2]) for x in s[:8]] == [16, 16, 16, 16, 16, 16, 4, 4]
-    assert out.count("call (__agret), __agile_guard_check") == n_acc
+    calls = 2 * n_acc if policy == "remap" else n_acc     # remap re-checks address | mask
+    assert out.count("call (__agret), __agile_guard_check") == calls
     loads = sum(1 for x in s if x[1].startswith("ld."))
     stores = n_acc - loads
     if policy == "trap":
@@ -59,6 +60,30 @@ def test_stream_kernels_every_access_guarded(policy):
         assert out.count("@%__agp4 st.global") == stores                            # predicated
     if policy == "sink":
         assert out.count("selp.b64 %__agd5, %__agd0, %__agT4, %__agp3") == stores  # sink page
+    assemble(out)
+
+
+def test_remap_policy_emission():
+    """REMAP_OR: each denied access re-checks address | mask (header offset 104) with
+    logging off; loads fall back to the zero page, stores and atomics are predicated on
+    either check, and a dropped atomic's destination is zeroed before the original
+    predicate joins in."""
+    out, rep = ag.agile_guard_instrument_ptx(STREAM, "remap")
+    n = rep["guarded"]
+    assert n == 28
+    assert out.count("ld.global.u64 %__agd6, [%__agT7+104];") == n
+    assert out.count("st.param.b32 [__agl], 0;") == n and out.count("st.param.b32 [__agl], 1;") == n
+    loads = len(re.findall(r"\bld\.global\.", STREAM))
+    assert out.count("selp.b64 %__agd5, %__agd5, %__agT3, %__agp4") == loads
+    assert out.count("@%__agp4 st.global") == n - loads
+    assemble(out)
+    body = """
+    setp.ne.u64 %p1, %rd1, 0;
+    @%p1 atom.global.add.u32 %r1, [%rd1], 1;
+    """
+    out, _ = ag.agile_guard_instrument_ptx(kernel(body), "remap")
+    zero, join = out.index("@!%__agp4 mov.b32 %r1, 0;"), out.index("and.pred %__agp4, %__agp4, %p1;")
+    assert zero < join and "@%__agp4 atom.global.add.u32 %r1, [%__agd5], 1;" in out
     assemble(out)
 
 
