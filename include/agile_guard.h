@@ -123,6 +123,12 @@ typedef struct {
                                  last byte - lo, rank (0 MMIO, 1 protected, 2 user), id};
                                  else NULL                                              */
     uint64_t remap_or;        /* mask the REMAP_OR policy ORs into a denied address     */
+    const uint32_t *ubits;    /* all-user block bitmap (device): bit k of word k / 32 set
+                                 iff bytes [lo + k B, lo + (k+1) B) lie inside one user
+                                 range, B = 2^ubits_log2 (chosen so that the bitmap is at
+                                 most 32 KiB); ubits_n + 1 bits, the last always clear  */
+    uint32_t ubits_log2;
+    uint32_t ubits_n;         /* blocks covering the window                             */
 } agile_dev_table_t;
 
 /* Decoded violation log. The first fault is the violating access with the smallest

@@ -44,7 +44,8 @@ class _DevTable(ctypes.Structure):
                 ("zero_page", ctypes.c_void_p), ("sink_page", ctypes.c_void_p),
                 ("bytes", ctypes.c_uint64), ("search_steps", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("crange", ctypes.c_void_p),
-                ("remap_or", ctypes.c_uint64)]
+                ("remap_or", ctypes.c_uint64), ("ubits", ctypes.c_void_p),
+                ("ubits_log2", ctypes.c_uint32), ("ubits_n", ctypes.c_uint32)]
 
 
 class _Record(ctypes.Structure):

@@ -22,6 +22,9 @@ struct agile_guard_table {
     size_t off_base = 0, off_end = 0, off_kind = 0, off_id = 0, total = 0;
     bool compact = false;                 // window < 4 GiB: packed 32-bit records exist
     size_t off_crange = 0;
+    size_t off_ubits = 0;
+    uint32_t ubits_log2 = 12;
+    uint32_t ubits_n = 0;
 };
 
 namespace agile {

@@ -70,13 +70,15 @@ struct TView {
     const uint64_t *base, *end;
     const uint32_t *kind, *id;
     const uint4 *crange;        // {start - lo, last - lo, rank, id} (windows under 4 GiB), or NULL
+    const uint32_t *ubits;      // all-user block bitmap (un + 1 bits, the last clear)
+    uint32_t ulg, un;           // block size 2^ulg, blocks in the window
 };
 
 __device__ __forceinline__ TView view_of(const agile_dev_table_t &T) {
     const uint64_t G = 1ull << T.log2_page;
     return TView{T.lo, T.npages, G - 1, T.lo + (T.npages << T.log2_page) - 1, T.log2_page, T.n,
                  T.search_steps, T.page, T.base, T.end, T.kind, T.id,
-                 reinterpret_cast<const uint4 *>(T.crange)};
+                 reinterpret_cast<const uint4 *>(T.crange), T.ubits, T.ubits_log2, T.ubits_n};
 }
 
 __device__ __forceinline__ uint32_t deny_of_kind(uint32_t kind) {
@@ -164,6 +166,22 @@ static __device__ __noinline__ uint32_t classify_slow(const TView &V, uint64_t a
 __device__ __forceinline__ uint32_t page_entry(const TView &V, uint64_t a) {
     const uint64_t p = (a - V.lo) >> V.lg;
     return p < V.npages ? V.page[p] : ~0u;
+}
+
+// Word of the all-user bitmap that holds a's block, shifted so that bit 0 is that block's
+// bit; addresses outside the window read the last (always clear) bit.
+__device__ __forceinline__ uint32_t user_bits(const TView &V, uint64_t a) {
+    const uint64_t k0 = (a - V.lo) >> V.ulg;
+    const uint32_t k = k0 < V.un ? (uint32_t)k0 : V.un;
+    return V.ubits[k >> 5] >> (k & 31);
+}
+
+// [a, a + w) lies inside one user allocation when its block is all-user (bits =
+// user_bits(V, a)) and the access does not run past that block's end. Branch-free; false
+// means "not decided here".
+__device__ __forceinline__ bool block_user_fast(const TView &V, uint64_t a, uint32_t w, uint32_t bits) {
+    const uint64_t m = (1ull << V.ulg) - 1;
+    return (bits & 1u) && ((a - V.lo) & m) + w <= m + 1;
 }
 
 // [a, a + bytes) lies inside one user allocation when the pages of its first and last
@@ -297,18 +315,27 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-// Shared-memory staging modes chosen by the host: nothing, the page map, or the page map
-// and the range arrays.
-enum : int { STAGE_NONE = 0, STAGE_PAGES = 1, STAGE_ALL = 2, STAGE_COMPACT = 3 };
+// Shared-memory staging, chosen by the host as a set of sections: the page map, the
+// range arrays, the packed records, the all-user bitmap. Laid out in that order.
+enum : int { ST_PAGES = 1, ST_RANGES = 2, ST_COMPACT = 4, ST_BITS = 8 };
+enum : int {
+    STAGE_NONE = 0, STAGE_PAGES = ST_PAGES, STAGE_ALL = ST_PAGES | ST_RANGES,
+    STAGE_COMPACT = ST_PAGES | ST_COMPACT, STAGE_BITS = ST_BITS
+};
 
 __host__ __device__ inline uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
+__host__ __device__ inline uint32_t ubits_bytes(const agile_dev_table_t &T) {
+    return round16(((uint64_t)T.ubits_n + 1 + 31) / 32 * 4);
+}
+
 // Bytes of shared memory a staging mode needs for table T.
 __host__ __device__ inline uint32_t stage_bytes(const agile_dev_table_t &T, int mode) {
-    if (mode == STAGE_NONE) return 0;
-    uint32_t b = round16((T.npages + 1) * 4);
-    if (mode == STAGE_ALL) b += 2 * round16(T.n * 8ull) + 2 * round16(T.n * 4ull);
-    if (mode == STAGE_COMPACT) b += round16(T.n * 16ull);       // packed records
+    uint32_t b = 0;
+    if (mode & ST_PAGES) b += round16((T.npages + 1) * 4);
+    if (mode & ST_RANGES) b += 2 * round16(T.n * 8ull) + 2 * round16(T.n * 4ull);
+    if (mode & ST_COMPACT) b += round16(T.n * 16ull);       // packed records
+    if (mode & ST_BITS) b += ubits_bytes(T);
     return b;
 }
 
@@ -330,14 +357,20 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
                                     unsigned long long *s_bar, LogDev *log) {
     TView V = view_of(T);
     if constexpr (MODE == STAGE_NONE) return V;
-    const uint32_t pb = round16((T.npages + 1) * 4);
+    constexpr bool kPages = MODE & ST_PAGES, kRanges = MODE & ST_RANGES;
+    constexpr bool kCompact = MODE & ST_COMPACT, kBits = MODE & ST_BITS;
+    const uint32_t pb = kPages ? round16((T.npages + 1) * 4) : 0;
     const uint32_t bb = round16(T.n * 8ull), kb = round16(T.n * 4ull);
+    const uint32_t rb = kRanges ? 2 * bb + 2 * kb : 0;
+    const uint32_t cb = kCompact ? round16(T.n * 16ull) : 0;
+    const uint32_t ub = kBits ? ubits_bytes(T) : 0;
     uint32_t *s_page = reinterpret_cast<uint32_t *>(smem);
     uint64_t *s_base = reinterpret_cast<uint64_t *>(smem + pb);
     uint64_t *s_end = reinterpret_cast<uint64_t *>(smem + pb + bb);
     uint32_t *s_kind = reinterpret_cast<uint32_t *>(smem + pb + 2 * bb);
     uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + pb + 2 * bb + kb);
-    uint4 *s_cr = reinterpret_cast<uint4 *>(smem + pb);                 // STAGE_COMPACT layout
+    uint4 *s_cr = reinterpret_cast<uint4 *>(smem + pb + rb);
+    uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + pb + rb + cb);
     const uint32_t bar = smem_addr(s_bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -345,37 +378,39 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t total = MODE == STAGE_ALL ? pb + 2 * bb + 2 * kb
-                             : MODE == STAGE_COMPACT ? pb + round16(T.n * 16ull) : pb;
+        const uint32_t total = pb + (T.n > 0 ? rb + cb : 0) + ub;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total)
                      : "memory");
-        bulk_g2s(s_page, T.page, pb, bar);
-        if (MODE == STAGE_ALL && T.n > 0) {
+        if (kPages) bulk_g2s(s_page, T.page, pb, bar);
+        if (kRanges && T.n > 0) {
             bulk_g2s(s_base, T.base, bb, bar);
             bulk_g2s(s_end, T.end, bb, bar);
             bulk_g2s(s_kind, T.kind, kb, bar);
             bulk_g2s(s_id, T.id, kb, bar);
         }
-        if (MODE == STAGE_COMPACT && T.n > 0) bulk_g2s(s_cr, T.crange, round16(T.n * 16ull), bar);
+        if (kCompact && T.n > 0) bulk_g2s(s_cr, T.crange, cb, bar);
+        if (kBits) bulk_g2s(s_bits, T.ubits, ub, bar);
     }
     if (!mbar_wait(bar, 0)) {               // (block-uniform only by timing: any thread may)
         if (log != nullptr && threadIdx.x == 0) atomicOr(&log->status, AGILE_LOG_STATUS_TIMEOUT);
         mbar_wait(bar, 0);                  // let copies in flight land, then copy by hand:
         for (uint32_t i = threadIdx.x; i < pb / 4; i += blockDim.x) s_page[i] = T.page[i];
-        if (MODE == STAGE_ALL)              // identical bytes, so a late bulk write is harmless
+        if (kRanges)                        // identical bytes, so a late bulk write is harmless
             for (uint32_t i = threadIdx.x; i < T.n; i += blockDim.x) {
                 s_base[i] = T.base[i]; s_end[i] = T.end[i]; s_kind[i] = T.kind[i]; s_id[i] = T.id[i];
             }
-        if (MODE == STAGE_COMPACT)
+        if (kCompact)
             for (uint32_t i = threadIdx.x; i < T.n; i += blockDim.x)
                 s_cr[i] = reinterpret_cast<const uint4 *>(T.crange)[i];
+        for (uint32_t i = threadIdx.x; i < ub / 4; i += blockDim.x) s_bits[i] = T.ubits[i];
     }
     __syncthreads();
-    V.page = s_page;
-    if constexpr (MODE == STAGE_ALL) {
+    if constexpr (kPages) V.page = s_page;
+    if constexpr (kRanges) {
         V.base = s_base; V.end = s_end; V.kind = s_kind; V.id = s_id;
     }
-    if constexpr (MODE == STAGE_COMPACT) V.crange = s_cr;
+    if constexpr (kCompact) V.crange = s_cr;
+    if constexpr (kBits) V.ubits = s_bits;
     return V;
 }
 
@@ -427,14 +462,19 @@ __device__ inline void slots_flush(LogDev *L, WarpSlots &S) {
     }
 }
 
-// Host side: pick the staging mode for a table (96 KiB for everything, 48 KiB for pages).
-// want_compact: the kernel has a 32-bit path and the table carries the compact arrays.
-inline int stage_mode(const agile_dev_table_t &T, bool want_ranges, bool want_compact = false) {
+// Host side: pick the staging mode for a table (96 KiB for everything, 48 KiB for pages
+// alone). want_compact: the kernel has a 32-bit path and the table carries the compact
+// arrays; want_bits: the kernel tests single accesses against the all-user bitmap, staged
+// with the page map (within 96 KiB) or alone (within 48 KiB) when the map does not fit.
+inline int stage_mode(const agile_dev_table_t &T, bool want_ranges, bool want_compact = false,
+                      bool want_bits = false) {
     if (T.npages == 0) return STAGE_NONE;
     if (want_compact && T.crange != nullptr && stage_bytes(T, STAGE_COMPACT) <= 96 * 1024)
         return STAGE_COMPACT;
-    if (want_ranges && stage_bytes(T, STAGE_ALL) <= 96 * 1024) return STAGE_ALL;
-    if (stage_bytes(T, STAGE_PAGES) <= 48 * 1024) return STAGE_PAGES;
+    const int b = want_bits ? ST_BITS : 0;
+    if (want_ranges && stage_bytes(T, STAGE_ALL | b) <= 96 * 1024) return STAGE_ALL | b;
+    if (stage_bytes(T, STAGE_PAGES | b) <= (want_bits ? 96 : 48) * 1024) return STAGE_PAGES | b;
+    if (want_bits && stage_bytes(T, STAGE_BITS) <= 48 * 1024) return STAGE_BITS;
     return STAGE_NONE;
 }
 

@@ -11,10 +11,12 @@ using agile::LaneLog;
 using agile::LogDev;
 using agile::TView;
 
-constexpr int kThreads = 512;
+// One 1024-thread block per SM: the staged bitmap is held once per SM, leaving the rest
+// of the unified L1/shared storage to L1, which caches the hot set of skewed gathers.
+constexpr int kThreads = 1024;
 
 template <int KIND, bool GUARD, int MODE, int POLICY>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 k_irregular(const agile_dev_table_t T, const int64_t *__restrict__ idx, float *base,
             float *__restrict__ out, size_t n, LogDev *log) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -41,7 +43,7 @@ int launch(const agile_dev_table_t &T, const int64_t *idx, void *base, float *ou
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     }
     size_t want = ((n >> 2) + kThreads - 1) / kThreads;
-    size_t cap = (size_t)agile::sm_count() * 2;
+    size_t cap = (size_t)agile::sm_count();
     unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
     k_irregular<KIND, GUARD, MODE, POLICY><<<blocks, kThreads, smem, st>>>(
         T, idx, reinterpret_cast<float *>(base), out, n, log);
@@ -52,11 +54,11 @@ int launch(const agile_dev_table_t &T, const int64_t *idx, void *base, float *ou
 template <int KIND, int POLICY>
 int by_mode(const agile_dev_table_t &T, const int64_t *idx, void *base, float *out, size_t n,
             LogDev *log, cudaStream_t st) {
-    switch (agile::stage_mode(T, true)) {
-        case agile::STAGE_ALL: return launch<KIND, true, agile::STAGE_ALL, POLICY>(T, idx, base, out, n, log, st);
-        case agile::STAGE_PAGES: return launch<KIND, true, agile::STAGE_PAGES, POLICY>(T, idx, base, out, n, log, st);
-        default: return launch<KIND, true, agile::STAGE_NONE, POLICY>(T, idx, base, out, n, log, st);
-    }
+    // Only the all-user bitmap is staged (at most 32 KiB): it decides nearly every access,
+    // and the page map and ranges, used on the slow path, are read through L1.
+    if (T.npages != 0 && agile::stage_bytes(T, agile::STAGE_BITS) <= 48 * 1024)
+        return launch<KIND, true, agile::STAGE_BITS, POLICY>(T, idx, base, out, n, log, st);
+    return launch<KIND, true, agile::STAGE_NONE, POLICY>(T, idx, base, out, n, log, st);
 }
 
 template <int KIND>

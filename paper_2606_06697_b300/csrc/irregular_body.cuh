@@ -90,14 +90,20 @@ __device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_
     const bool act = u < n4;
     bool ok0 = true, ok1 = true, oko = true;
     if constexpr (GUARD) {
+        // A warp's span that stays inside one all-user block is decided by one bitmap word
+        // (shared memory when staged); other spans by the page map.
         const bool full = spans && u0 + 32 <= n4;
-        const bool fast_i = full && span_allowed(V, (uint64_t)(idx2 + 2 * u0), 1024);
+        const uint64_t si = (uint64_t)(idx2 + 2 * u0);
+        const bool fast_i = full && (block_user_fast(V, si, 1024, user_bits(V, si)) ||
+                                     span_allowed(V, si, 1024));
         if (!fast_i && act) {
             ok0 = lane_check(V, (uint64_t)(idx2 + 2 * u), 16, 0, ll);
             ok1 = lane_check(V, (uint64_t)(idx2 + 2 * u + 1), 16, 1, ll);
         }
         if constexpr (kGather) {
-            const bool fast_o = full && span_allowed(V, (uint64_t)(out4 + u0), 512);
+            const uint64_t so = (uint64_t)(out4 + u0);
+            const bool fast_o = full && (block_user_fast(V, so, 512, user_bits(V, so)) ||
+                                         span_allowed(V, so, 512));
             if (!fast_o && act) oko = lane_check(V, (uint64_t)(out4 + u), 16, 3, ll);
         }
     }
@@ -106,13 +112,29 @@ __device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_
     const longlong2 p1 = __ldg(load_src<POLICY>(V, T, idx2 + 2 * u + 1, ok1, 16));
     (void)zero2;
     const int64_t e[4] = {p0.x, p0.y, p1.x, p1.y};
-    float v[4];
+    float *addr[4];
+    bool ok[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        float *addr = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e[k]);
-        const bool ok = !GUARD || lane_check(V, (uint64_t)addr, 4, 2, ll);
-        v[k] = element<KIND, POLICY>(V, addr, ok, e[k], T);
+        addr[k] = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e[k]);
+        ok[k] = true;
     }
+    if constexpr (GUARD) {
+        // The four all-user bitmap words are read before any is used, so their latencies
+        // overlap; an element in an all-user block is then decided without a branch, the
+        // rest (blocks that are not all user, denials) by the full classification.
+        uint32_t pe[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pe[k] = user_bits(V, (uint64_t)addr[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ok[k] = block_user_fast(V, (uint64_t)addr[k], 4, pe[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (!ok[k]) ok[k] = lane_check(V, (uint64_t)addr[k], 4, 2, ll);
+    }
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = element<KIND, POLICY>(V, addr[k], ok[k], e[k], T);
     if constexpr (kGather) {
         const float4 o = make_float4(v[0], v[1], v[2], v[3]);
         if (oko || kAlways) {

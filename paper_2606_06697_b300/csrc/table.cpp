@@ -141,8 +141,29 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
             t->off_crange = off;
             off += align256(n * 16);
         }
+        // All-user block bitmap for single-access fast tests: blocks of B = 2^ubits_log2
+        // bytes from lo (at least 4 KiB, as small as keeps the bitmap within 2^18 bits),
+        // a bit set iff its block lies inside one user range.
+        const uint64_t window = t->npages << lg;            // < 2^64: lo + window - 1 fits
+        uint32_t ulg = 12;
+        while (ulg < 63 && (window >> ulg) + ((window & ((1ull << ulg) - 1)) != 0) > (1ull << 18)) ++ulg;
+        t->ubits_log2 = ulg;
+        t->ubits_n = (uint32_t)((window >> ulg) + ((window & ((1ull << ulg) - 1)) != 0));
+        t->off_ubits = off;
+        off += align256(((uint64_t)t->ubits_n + 1 + 31) / 32 * 4);
         t->total = off;
         t->staging.assign(t->total, 0);
+        {
+            uint32_t *ub = reinterpret_cast<uint32_t *>(t->staging.data() + t->off_ubits);
+            const uint64_t B = 1ull << ulg;
+            for (size_t i = 0; i < n; ++i) {
+                if (t->kind[i] != AGILE_USER) continue;
+                const uint64_t b = t->base[i] - t->lo, e = t->end[i] - t->lo;
+                uint64_t k = b / B + (b % B != 0);              // first block starting in it
+                const uint64_t k_end = std::min<uint64_t>(e / B, t->ubits_n);  // blocks ending in it
+                for (; k < k_end; ++k) ub[k >> 5] |= 1u << (k & 31);
+            }
+        }
         std::memcpy(t->staging.data() + kPageOff, t->page.data(), t->page.size() * 4);
         if (n) {
             std::memcpy(t->staging.data() + t->off_base, t->base.data(), n * 8);
@@ -212,6 +233,9 @@ int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, 
     h.search_steps = t->search_steps;
     h.remap_or = t->remap_or;
     if (t->compact) h.crange = (const uint32_t *)(d + t->off_crange);
+    h.ubits = (const uint32_t *)(d + t->off_ubits);
+    h.ubits_log2 = t->ubits_log2;
+    h.ubits_n = t->ubits_n;
     static_assert(sizeof(agile_dev_table_t) <= kHeaderBytes, "header fits");
     std::memcpy(t->staging.data(), &h, sizeof h);
     std::memset(t->staging.data() + kZeroOff, 0, 128);
