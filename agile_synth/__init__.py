@@ -151,6 +151,39 @@ def table1_apertures() -> Ranges:
                    [KIND_MMIO, KIND_PROTECTED, KIND_USER], [2, 1, 0])
 
 
+def table1_protected() -> Ranges:
+    """Table I's two protected apertures (MMIO, then kernel/module memory): the aperture
+    set of the aperture-only rule."""
+    (m0, m1), (p0, p1) = TABLE1_MMIO, TABLE1_PROTECTED
+    return _ranges([m0, p0], [m1 - m0, p1 - p0], [KIND_MMIO, KIND_PROTECTED], [2, 1])
+
+
+def aperture_accesses(n: int, seed: int = SEED_BASE + 7):
+    """(address, width, label) against Table I's protected apertures: 90% inside the user
+    aperture, 4% inside the kernel/module aperture, 3% inside the MMIO aperture and 3%
+    across an aperture edge (the lower MMIO edge and the MMIO/protected edge, labelled
+    MMIO; the protected/user edge, labelled PROTECTED; equal thirds). Shuffled."""
+    st = Stream(seed, 11)
+    n_p, n_m, n_e = int(n * 0.04), int(n * 0.03), int(n * 0.03)
+    n_ok = n - n_p - n_m - n_e
+    parts = []
+    for cnt, (lo, hi), lab in ((n_ok, TABLE1_USER, LABEL_ALLOW), (n_p, TABLE1_PROTECTED, LABEL_PROTECTED),
+                               (n_m, TABLE1_MMIO, LABEL_MMIO)):
+        w = st.choice(WIDTHS, cnt).astype(np.int64)
+        parts.append((lo + st.below(hi - lo - w + 1, cnt), w, np.full(cnt, lab, np.uint8)))
+    w = st.choice(WIDTHS[1:], n_e).astype(np.int64)
+    k = 1 + st.below(w - 1, n_e)
+    which = st.below(3, n_e)
+    edge = np.array([TABLE1_MMIO[0], TABLE1_MMIO[1], TABLE1_PROTECTED[1]], dtype=np.int64)[which]
+    lab = np.where(which == 2, LABEL_PROTECTED, LABEL_MMIO).astype(np.uint8)
+    parts.append((edge - k, w, lab))
+    addr = np.concatenate([p[0] for p in parts])
+    width = np.concatenate([p[1] for p in parts]).astype(np.uint8)
+    label = np.concatenate([p[2] for p in parts])
+    p = st.permutation(n)
+    return addr[p].astype(U64), width[p], label[p]
+
+
 def _round_up(x, m):
     return (x + m - 1) // m * m
 

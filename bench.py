@@ -573,7 +573,9 @@ def batch_throughput(ag, torch, dev, stream, sizes=(1 << 20, 1 << 28), reps=None
                      log2_pages=(12, 16, 21)):
     """Batch check (10 B/check: 8 address + 1 width in, 1 verdict out) on the 84-range
     table workload, at each page size; inputs replicated from 1M generated accesses, L2
-    flushed before every launch. Returns per size and page size, plus the best page size."""
+    flushed before every launch. Returns per size and page size, plus the best page size,
+    and beside them the aperture-only rule (Table I's two protected apertures) on the
+    aperture workload of the same size."""
     t = syn.batch_table()
     log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
     tabs = {}
@@ -610,7 +612,27 @@ def batch_throughput(ag, torch, dev, stream, sizes=(1 << 20, 1 << 28), reps=None
             res[f"page_2^{lg}"] = {"checks_per_s": n / (ms / 1e3), "ms": ms,
                                    "gbs": n * 10 / (ms / 1e3) / 1e9}
         best = min(res, key=lambda k: res[k]["ms"])
-        out[name] = dict(res, best=best, bytes_per_check=10)
+        a_addr, a_width, _ = syn.aperture_accesses(m)
+        da.copy_(torch.from_numpy(a_addr.view(np.int64)).to(dev).repeat((n + m - 1) // m)[:n])
+        dw.copy_(torch.from_numpy(a_width).to(dev).repeat((n + m - 1) // m)[:n])
+        apset = syn.table1_protected()
+        tot = 0.0
+        for i in range(nrep + 3):
+            flush.fill_(i & 0xFF)
+            ag.agile_violation_log_init(log, 0, stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                ag.agile_aperture_check_batch((apset.base, apset.size, apset.kind, apset.ident),
+                                              da, dw, n, dv, log, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                tot += e0.elapsed_time(e1)
+        ms = tot / nrep
+        aperture = {"checks_per_s": n / (ms / 1e3), "ms": ms, "gbs": n * 10 / (ms / 1e3) / 1e9}
+        out[name] = dict(res, best=best, bytes_per_check=10, aperture_rule=aperture)
         del da, dw, dv
     return out
 

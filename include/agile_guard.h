@@ -226,6 +226,21 @@ AGILE_API int agile_guard_check_batch(const agile_dev_table_t *tbl, const uint64
                             const uint8_t *d_width, size_t n, uint8_t *d_verdict, void *d_log,
                             void *stream);
 
+/* Aperture-only batched check (Table I; Sec. V-E: the paper's PTX guard tests accesses
+ * against the protected I/O and kernel/module intervals only, leaving every other access
+ * on the normal path). verdict[i] is INVALID as for agile_guard_check_batch; MMIO if the
+ * access shares a byte with an MMIO aperture, else PROTECTED if it shares a byte with a
+ * protected aperture (the lowest-based such aperture is reported); else ALLOW -- holes,
+ * straddles and freed memory are not seen by this rule. h_apertures: host array of at
+ * most AGILE_MAX_APERTURES non-empty, pairwise disjoint ranges of kind PROTECTED or MMIO,
+ * copied into the launch. Logging, layouts and alignment as for agile_guard_check_batch.
+ * Errors: INVALID_ARG, TOO_LARGE, BAD_KIND (a user aperture), ZERO_SIZE, RANGE_OVERFLOW,
+ * OVERLAP, ALIGN (d_log). */
+#define AGILE_MAX_APERTURES 4
+AGILE_API int agile_aperture_check_batch(const agile_range_t *h_apertures, size_t n_apertures,
+                                         const uint64_t *d_addr, const uint8_t *d_width, size_t n,
+                                         uint8_t *d_verdict, void *d_log, void *stream);
+
 /* ---------------------------------------------------------------- guarded kernels */
 
 enum { AGILE_OP_COPY = 0, AGILE_OP_SCALE = 1, AGILE_OP_TRIAD = 2 };

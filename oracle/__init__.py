@@ -109,6 +109,23 @@ def check_batch(r, addr: np.ndarray, width: np.ndarray, method: str = "linear"):
     return verdict, rid, Log._of(log)
 
 
+def aperture_batch(apertures, addr: np.ndarray, width: np.ndarray):
+    """Aperture rule (Table I, Sec. V-E): deny only accesses that share a byte with a
+    protected or MMIO aperture (MMIO first, lowest base), INVALID as in check_batch,
+    everything else allowed. Returns (verdict, range id, Log); key = access index."""
+    base, size, kind, ident = _table(apertures)
+    addr = np.ascontiguousarray(addr, dtype=np.uint64)
+    width = np.ascontiguousarray(width, dtype=np.uint8)
+    m = len(addr)
+    verdict = np.empty(m, dtype=np.uint8)
+    rid = np.empty(m, dtype=np.uint32)
+    log = _Log()
+    _L().orc_aperture_batch(ctypes.c_size_t(len(base)), _p(base), _p(size), _p(kind), _p(ident),
+                            ctypes.c_size_t(m), _p(addr), _p(width), _p(verdict), _p(rid),
+                            ctypes.byref(log))
+    return verdict, rid, Log._of(log)
+
+
 def validate(r, ptr: np.ndarray, nbytes: np.ndarray):
     """API-time pointer validation, Sec. IV-E and V-C: a (pointer, byte count) passes
     only when the whole byte range lies inside one live user allocation."""

@@ -215,6 +215,51 @@ void orc_check_batch(size_t n, const uint64_t *base, const uint64_t *size, const
     if (s) sorted_free(s);
 }
 
+/* Aperture rule (Table I; Sec. V-E: the PTX guard tests an access against the protected
+ * I/O and kernel/module intervals only, leaving everything else on the normal path).
+ * The apertures are protected or MMIO ranges; an access is
+ *   INVALID  as in step 1 of the table rule (batch widths 1, 2, 4, 8, 16 only),
+ *   MMIO     if it shares a byte with an MMIO aperture,
+ *   PROTECTED if it shares a byte with a protected aperture,
+ *   ALLOW    otherwise (holes, straddles and freed memory are not seen by this rule),
+ * reporting the lowest-based aperture of the deciding kind. */
+static uint32_t classify_aperture(const orc_table *t, uint64_t a, uint64_t w, uint32_t *rid) {
+    *rid = NO_RANGE;
+    if (!end_ok(a, w)) return V_INVALID;
+    static const uint32_t order[2] = {K_MMIO, K_PROTECTED};
+    static const uint32_t verdict[2] = {V_MMIO, V_PROTECTED};
+    for (int c = 0; c < 2; ++c) {
+        int found = 0;
+        uint64_t lowest = 0;
+        for (size_t j = 0; j < t->n; ++j)
+            if (t->kind[j] == order[c] && overlaps(a, w, t->base[j], t->size[j]) &&
+                (!found || t->base[j] < lowest)) {
+                found = 1;
+                lowest = t->base[j];
+                *rid = t->id[j];
+            }
+        if (found) return verdict[c];
+    }
+    return V_ALLOW;
+}
+
+/* Aperture batch check: as orc_check_batch under the aperture rule. */
+void orc_aperture_batch(size_t n, const uint64_t *base, const uint64_t *size, const uint32_t *kind,
+                        const uint32_t *id, size_t m, const uint64_t *addr, const uint8_t *width,
+                        uint8_t *verdict, uint32_t *rid_out, orc_log *log) {
+    orc_table t = {n, base, size, kind, id};
+    log_clear(log);
+    for (size_t i = 0; i < m; ++i) {
+        uint64_t w = width[i];
+        uint32_t rid = NO_RANGE, v;
+        if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16)) v = V_INVALID;
+        else v = classify_aperture(&t, addr[i], w, &rid);
+        verdict[i] = (uint8_t)v;
+        if (rid_out) rid_out[i] = rid;
+        if (v != V_ALLOW) log_note(log, i, addr[i], (uint32_t)w, v, 0, rid);
+    }
+}
+
 /* API-time pointer validation (Sec. IV-E, V-C): (pointer, byte count) pairs, any size. */
 void orc_validate(size_t n, const uint64_t *base, const uint64_t *size, const uint32_t *kind,
                   const uint32_t *id, size_t m, const uint64_t *ptr, const uint64_t *bytes,

@@ -118,6 +118,8 @@ _SIG = {
     "agile_violation_log_init": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
     "agile_violation_log_read": (ctypes.c_int, [_P, _P, _P]),
     "agile_guard_check_batch": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+    "agile_aperture_check_batch": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P, ctypes.c_size_t,
+                                                  _P, _P, _P]),
     "agile_stream_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
                                            ctypes.c_float, ctypes.c_int, _P, _P]),
     "agile_irregular_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
@@ -269,8 +271,7 @@ class Table:
         return DevTable(v, buf)
 
 
-def agile_guard_table_build(base, size, kind, ident, log2_page: int = 21) -> Table:
-    """Build a table from parallel arrays (any order)."""
+def _range_array(base, size, kind, ident):
     base = _np(base, np.uint64)
     n = len(base)
     arr = (_Range * max(n, 1))()
@@ -281,6 +282,12 @@ def agile_guard_table_build(base, size, kind, ident, log2_page: int = 21) -> Tab
         raw["size"] = _np(size, np.uint64)
         raw["kind"] = _np(kind, np.uint32)
         raw["id"] = _np(ident, np.uint32)
+    return arr, n
+
+
+def agile_guard_table_build(base, size, kind, ident, log2_page: int = 21) -> Table:
+    """Build a table from parallel arrays (any order)."""
+    arr, n = _range_array(base, size, kind, ident)
     out = ctypes.c_void_p()
     _check(lib().agile_guard_table_build(arr, n, log2_page, ctypes.byref(out)),
            "agile_guard_table_build")
@@ -349,6 +356,15 @@ def agile_guard_check_batch(dev: DevTable, d_addr, d_width, n: int, d_verdict, d
     _check(lib().agile_guard_check_batch(dev.ref, _dptr(d_addr), _dptr(d_width), n,
                                          _dptr(d_verdict), _dptr(d_log), _stream(stream)),
            "agile_guard_check_batch")
+
+
+def agile_aperture_check_batch(apertures, d_addr, d_width, n: int, d_verdict, d_log=None,
+                               stream=None) -> None:
+    """apertures: (base, size, kind, ident) parallel arrays, at most AGILE_MAX_APERTURES."""
+    arr, m = _range_array(*apertures)
+    _check(lib().agile_aperture_check_batch(arr, m, _dptr(d_addr), _dptr(d_width), n,
+                                            _dptr(d_verdict), _dptr(d_log), _stream(stream)),
+           "agile_aperture_check_batch")
 
 
 def agile_stream_launch(op: str, dev: DevTable | None, d_a, d_b, d_c, n: int, s: float = 3.0,

@@ -126,14 +126,32 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
             uint64_t out = 0;
             uint32_t open = 0;                         // accesses left to the full rule
+            uint32_t rid0 = agile::kNoRange;           // range of the group's first denial
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
                 uint32_t v = 0, rid = agile::kNoRange;
                 const bool done = legal_width(w) && av[k] <= ~0ull - w && decide32(V, av[k], w, &v, &rid);
                 open |= (uint32_t)!done << k;
-                if (done && v != AGILE_ALLOW) ll.note(g * 8 + k, agile::pack_info(0, v, w, rid), av[k]);
+                rid0 = (out == 0 && v != AGILE_ALLOW) ? rid : rid0;
                 out |= (uint64_t)v << (8 * k);
+            }
+            if (out) {
+                // The group's decided denials, counted at once. A lane meets its groups in
+                // increasing index order, so only a lane's first denying group can hold its
+                // smallest key; the accesses left open are noted by the full rule below.
+                uint64_t m = out | (out >> 4);
+                m |= m >> 2;
+                m |= m >> 1;
+                m &= 0x0101010101010101ull;           // bit 8k set iff verdict k is a denial
+                if (ll.cnt == 0) {
+                    const int b = __ffsll((long long)m) - 1;
+                    ll.key = g * 8 + b / 8;
+                    ll.info = agile::pack_info(0, (uint32_t)(out >> b) & 0xFFu,
+                                               (uint32_t)(wv >> b) & 0xFFu, rid0);
+                    ll.addr = addr[g * 8 + b / 8];
+                }
+                ll.cnt += __popcll(m);
             }
 #pragma unroll 1
             for (; open; open &= open - 1) {           // rare: re-read the access, full rule

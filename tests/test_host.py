@@ -166,3 +166,18 @@ def test_validate_dma_matches_oracle(seed):
     ov, orid = oracle.validate_exact(t, ptr.astype(np.uint64), np.maximum(nb, 0).astype(np.uint64))
     assert (v == ov).all() and (rid == orid).all()
     assert (v == 0).any() and (v == 6).any()
+
+
+@pytest.mark.parametrize("bad,code", [
+    (syn._ranges([0xF0000000000] * 5, [16] * 5, [2] * 5, [1] * 5), -11),        # over the maximum
+    (syn._ranges([0x1000], [16], [syn.KIND_USER], [1]), -5),                     # a user aperture
+    (syn._ranges([0x1000, 0x1008], [16, 16], [syn.KIND_MMIO] * 2, [1, 2]), -2),  # overlap
+    (syn._ranges([0x1000], [0], [syn.KIND_MMIO], [1]), -3),                      # empty
+    (syn._ranges([2**64 - 8], [16], [syn.KIND_MMIO], [1]), -4),                  # end past 2^64 - 1
+])
+def test_aperture_set_rejected_before_launch(bad, code):
+    """The aperture set is validated on the host before anything reaches the device."""
+    with pytest.raises(ag.AgileError) as e:
+        ag.agile_aperture_check_batch((bad.base, bad.size, bad.kind, bad.ident), 0x1000, 0x2000, 8,
+                                      0x3000)
+    assert e.value.code == code

@@ -1,6 +1,7 @@
 """Pins for the oracle: checks against facts fixed outside the oracle itself.
 
-- Table I golden cases derived by hand (tests/golden/table1_apertures.txt).
+- Table I golden cases derived by hand (tests/golden/table1_apertures.txt), and for the
+  aperture rule (tests/golden/table1_aperture_rule.txt).
 - Brute force on tiny tables through a per-byte ownership formulation: every byte of a
   small window is assigned its owning range, and the verdict is read off the set of
   owners -- a different computation from the oracle's interval compares.
@@ -152,6 +153,96 @@ def test_bruteforce_tiny_tables(window_lo):
             i = int(viol[0])
             assert (log.key, log.addr, log.width, log.verdict, log.range_id) == \
                 (i, int(addrs[i]), int(widths[i]), int(bv[i]), int(brid[i]))
+
+
+# ---------------------------------------------------------------- aperture rule
+
+APERTURE_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_aperture_rule.txt")
+
+
+def test_aperture_rule_table1_golden():
+    rows = []
+    for line in open(APERTURE_GOLDEN):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            rows.append((int(f[1], 16), int(f[2], 0), V[f[3]], int(f[4], 16)))
+    addr = np.array([r[0] for r in rows], dtype=np.uint64)
+    width = np.array([r[1] for r in rows], dtype=np.uint8)
+    v, rid, log = oracle.aperture_batch(syn.table1_protected(), addr, width)
+    assert v.tolist() == [r[2] for r in rows]
+    assert rid.tolist() == [r[3] for r in rows]
+    first = next(i for i, r in enumerate(rows) if r[2] != 0)
+    assert log.key == first and log.count == sum(r[2] != 0 for r in rows)
+
+
+def test_aperture_workload_labels():
+    """The aperture workload places each access by construction; its verdicts are its labels."""
+    n = 1 << 20
+    addr, width, label = syn.aperture_accesses(n)
+    v, rid, log = oracle.aperture_batch(syn.table1_protected(), addr, width)
+    assert (v == label).all()
+    denied = int(n * 0.04) + 2 * int(n * 0.03)
+    assert int((label == 0).sum()) == n - denied and log.count == denied
+    assert log.key == int(np.flatnonzero(label)[0])
+
+
+@pytest.mark.parametrize("window_lo", [0x1000, 2**64 - 192])
+def test_aperture_rule_bruteforce(window_lo):
+    """Per-byte owners again: deny iff some byte belongs to an MMIO (first) or protected
+    aperture, reporting the lowest-based one; user ranges in the tiny tables are ignored."""
+    st = syn.Stream(13, window_lo & 0xFFFF)
+    for trial in range(40):
+        t = _tiny_table(st, window_lo)
+        keep = t.kind != syn.KIND_USER
+        ap = syn._ranges(t.base[keep], t.size[keep], t.kind[keep], t.ident[keep])
+        lo, hi = max(window_lo - 20, 0), min(window_lo + 196, M64)
+        addrs = np.repeat(np.arange(lo, hi, dtype=np.uint64), 6)
+        widths = np.tile(np.array([1, 2, 3, 4, 8, 16], dtype=np.uint8), hi - lo)
+        owner = {}
+        for j in range(len(ap)):
+            for x in range(int(ap.base[j]), int(ap.base[j] + ap.size[j])):
+                owner[x] = j
+        v, rid, log = oracle.aperture_batch(ap, addrs, widths)
+        for i, (a, w) in enumerate(zip(addrs.tolist(), widths.tolist())):
+            if w not in (1, 2, 4, 8, 16) or a + w > M64:
+                assert (v[i], rid[i]) == (V["INVALID"], oracle.NO_RANGE)
+                continue
+            hit = {owner[x] for x in range(a, a + w) if x in owner}
+            want = (V["ALLOW"], oracle.NO_RANGE)
+            for cls, name in ((syn.KIND_MMIO, "MMIO"), (syn.KIND_PROTECTED, "PROTECTED")):
+                js = [j for j in hit if ap.kind[j] == cls]
+                if js:
+                    j = min(js, key=lambda j: int(ap.base[j]))
+                    want = (V[name], int(ap.ident[j]))
+                    break
+            assert (int(v[i]), int(rid[i])) == want, (hex(a), w)
+        assert log.count == int((v != 0).sum())
+
+
+def test_aperture_rule_is_the_table_rule_with_user_complement():
+    """With the rest of the space given to user ranges, the table rule denies exactly what
+    the aperture rule denies (the batch workload's apertures, its own accesses)."""
+    t = syn.batch_table()
+    addr, width, label = syn.batch_accesses(t, 1 << 16)
+    keep = t.kind != syn.KIND_USER
+    ap = syn._ranges(t.base[keep], t.size[keep], t.kind[keep], t.ident[keep])
+    order = np.argsort(ap.base)
+    b, e = ap.base[order].astype(object), (ap.base[order] + ap.size[order]).astype(object)
+    ub, us = [], []
+    cur = 0
+    for x, y in zip(b, e):
+        if x > cur:
+            ub.append(cur); us.append(x - cur)
+        cur = y
+    ub.append(cur); us.append(M64 - cur)
+    full = syn._ranges(list(ap.base) + ub, list(ap.size) + us,
+                       list(ap.kind) + [syn.KIND_USER] * len(ub),
+                       list(ap.ident) + list(range(0x5000, 0x5000 + len(ub))))
+    va, ra, la = oracle.aperture_batch(ap, addr, width)
+    vt, rt, lt = oracle.check_batch(full, addr, width, method="sorted")
+    deny = va != 0
+    assert deny.sum() > 0 and (vt[deny] == va[deny]).all() and (rt[deny] == ra[deny]).all()
+    assert (vt[~deny] == 0).all()
 
 
 def test_table_rules():
