@@ -111,76 +111,76 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
     const size_t ngroups = n / VEC;
 
-    constexpr bool kC32 = MODE == agile::STAGE_COMPACT;
+    constexpr bool kC32 = (MODE & agile::ST_COMPACT) != 0;
     LaneLog ll;
-    for (size_t g = tid; g < ngroups; g += nthreads) {
-        if constexpr (VEC == 8 && kC32) {
-            const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
-            uint64_t av[8];
+    if constexpr (VEC == 8) {
+        const uint32_t lane = threadIdx.x & 31;
+        for (size_t g0 = tid - lane; g0 < ngroups; g0 += nthreads) {   // warp-uniform trip count
+            const size_t g = g0 + lane;
+            // Pass 1, branch-free: an access inside an all-user block of the bitmap is
+            // allowed. The others ("open") are decided in pass 2.
+            uint32_t open = 0;
+            if (g < ngroups) {
+                const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
+                uint64_t av[8];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {              // registers only: no indexed arrays
-                const uint4 q = __ldcs(pa + k);
-                av[2 * k] = (uint64_t)q.y << 32 | q.x;
-                av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
-            }
-            const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
-            uint64_t out = 0;
-            uint32_t open = 0;                         // accesses left to the full rule
-            uint32_t rid0 = agile::kNoRange;           // range of the group's first denial
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
-                uint32_t v = 0, rid = agile::kNoRange;
-                const bool done = legal_width(w) && av[k] <= ~0ull - w && decide32(V, av[k], w, &v, &rid);
-                open |= (uint32_t)!done << k;
-                rid0 = (out == 0 && v != AGILE_ALLOW) ? rid : rid0;
-                out |= (uint64_t)v << (8 * k);
-            }
-            if (out) {
-                // The group's decided denials, counted at once. A lane meets its groups in
-                // increasing index order, so only a lane's first denying group can hold its
-                // smallest key; the accesses left open are noted by the full rule below.
-                uint64_t m = out | (out >> 4);
-                m |= m >> 2;
-                m |= m >> 1;
-                m &= 0x0101010101010101ull;           // bit 8k set iff verdict k is a denial
-                if (ll.cnt == 0) {
-                    const int b = __ffsll((long long)m) - 1;
-                    ll.key = g * 8 + b / 8;
-                    ll.info = agile::pack_info(0, (uint32_t)(out >> b) & 0xFFu,
-                                               (uint32_t)(wv >> b) & 0xFFu, rid0);
-                    ll.addr = addr[g * 8 + b / 8];
+                for (int k = 0; k < 4; ++k) {          // registers only: no indexed arrays
+                    const uint4 q = __ldcs(pa + k);
+                    av[2 * k] = (uint64_t)q.y << 32 | q.x;
+                    av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
                 }
-                ll.cnt += __popcll(m);
-            }
-#pragma unroll 1
-            for (; open; open &= open - 1) {           // rare: re-read the access, full rule
-                const int k = __ffs(open) - 1;
-                const size_t i = g * 8 + k;
-                const uint64_t v = full_one<true>(V, addr[i], width[i], i, ll);
-                out = (out & ~(0xFFull << (8 * k))) | v << (8 * k);
-            }
-            __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), (unsigned long long)out);
-        } else if constexpr (VEC == 8) {
-            const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
-            uint64_t av[8];
+                const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint4 q = __ldcs(pa + k);
-                av[2 * k] = (uint64_t)q.y << 32 | q.x;
-                av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
+                    const bool ok = legal_width(w) && av[k] <= ~0ull - w &&
+                                    agile::block_user_fast(V, av[k], w, agile::user_bits(V, av[k]));
+                    open |= (uint32_t)!ok << k;
+                }
+                __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), 0ull);
             }
-            const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
-            uint64_t out = 0;
+            // Pass 2: the warp's open accesses are dealt out to its lanes, 32 at a time, so
+            // the full decision runs ceil(open / 32) times per warp rather than once for
+            // every position any lane has open.
+            const uint32_t c = __popc(open);
+            uint32_t incl = c;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
-                out |= (uint64_t)full_one<false>(V, av[k], w, g * 8 + k, ll) << (8 * k);
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(agile::kFull, incl, o);
+                if (lane >= (uint32_t)o) incl += t;
             }
-            __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), (unsigned long long)out);
-        } else {
-            verdict[g] = (uint8_t)full_one<kC32>(V, addr[g], width[g], g, ll);
+            const uint32_t total = __shfl_sync(agile::kFull, incl, 31);
+            const uint32_t excl = incl - c;
+            __syncwarp();                              // the zero stores above come first
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                uint32_t own = 0;                      // lanes whose open accesses all precede q
+#pragma unroll
+                for (int step = 16; step; step >>= 1) {
+                    const uint32_t t = __shfl_sync(agile::kFull, incl, own + step - 1);
+                    own = t <= q ? own + step : own;
+                }
+                const uint32_t omask = __shfl_sync(agile::kFull, open, own & 31);
+                const uint32_t oexcl = __shfl_sync(agile::kFull, excl, own & 31);
+                if (q < total) {
+                    uint32_t m = omask;
+                    for (uint32_t r = q - oexcl; r; --r) m &= m - 1;   // drop the earlier ones
+                    const int k = __ffs(m) - 1;
+                    const size_t i = (g0 + own) * 8 + k;
+                    const uint64_t a = addr[i];
+                    const uint32_t w = width[i];
+                    uint32_t v = 0, rid = agile::kNoRange;
+                    bool done = false;
+                    if constexpr (kC32) done = legal_width(w) && a <= ~0ull - w && decide32(V, a, w, &v, &rid);
+                    if (!done) v = full_one<kC32>(V, a, w, i, ll);
+                    else if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
+                    if (v != AGILE_ALLOW) verdict[i] = (uint8_t)v;
+                }
+            }
         }
+    } else {
+        for (size_t g = tid; g < ngroups; g += nthreads)
+            verdict[g] = (uint8_t)full_one<kC32>(V, addr[g], width[g], g, ll);
     }
     if (VEC > 1 && blockIdx.x == 0 && threadIdx.x < 32) {    // the last n % VEC accesses
         const size_t i = ngroups * VEC + threadIdx.x;
@@ -195,7 +195,7 @@ int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size
     const uint32_t smem = agile::stage_bytes(T, MODE);
     if (smem > 48 * 1024) {
         AGILE_CUDA_TRY(cudaFuncSetAttribute(k_check_batch<MODE, VEC>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     size_t groups = n / VEC;
     size_t want = (groups + kThreads - 1) / kThreads;
@@ -209,10 +209,16 @@ int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size
 template <int VEC>
 int launch_mode(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
                 uint8_t *v, LogDev *log, cudaStream_t st) {
-    switch (agile::stage_mode(T, true, true)) {
+    constexpr int kCB = agile::STAGE_COMPACT | agile::ST_BITS, kAB = agile::STAGE_ALL | agile::ST_BITS;
+    constexpr int kPB = agile::STAGE_PAGES | agile::ST_BITS;
+    switch (agile::stage_mode(T, true, true, true)) {
+        case kCB: return launch<kCB, VEC>(T, a, w, n, v, log, st);
         case agile::STAGE_COMPACT: return launch<agile::STAGE_COMPACT, VEC>(T, a, w, n, v, log, st);
+        case kAB: return launch<kAB, VEC>(T, a, w, n, v, log, st);
         case agile::STAGE_ALL: return launch<agile::STAGE_ALL, VEC>(T, a, w, n, v, log, st);
+        case kPB: return launch<kPB, VEC>(T, a, w, n, v, log, st);
         case agile::STAGE_PAGES: return launch<agile::STAGE_PAGES, VEC>(T, a, w, n, v, log, st);
+        case agile::STAGE_BITS: return launch<agile::STAGE_BITS, VEC>(T, a, w, n, v, log, st);
         default: return launch<agile::STAGE_NONE, VEC>(T, a, w, n, v, log, st);
     }
 }

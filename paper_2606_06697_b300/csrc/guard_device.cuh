@@ -462,16 +462,19 @@ __device__ inline void slots_flush(LogDev *L, WarpSlots &S) {
     }
 }
 
-// Host side: pick the staging mode for a table (96 KiB for everything, 48 KiB for pages
-// alone). want_compact: the kernel has a 32-bit path and the table carries the compact
+// Host side: pick the staging mode for a table (96 KiB for everything -- 104 KiB for the
+// packed records with the bitmap, two blocks of 512 threads still fitting on an SM --
+// 48 KiB for pages alone). want_compact: the kernel has a 32-bit path and the table carries the compact
 // arrays; want_bits: the kernel tests single accesses against the all-user bitmap, staged
 // with the page map (within 96 KiB) or alone (within 48 KiB) when the map does not fit.
 inline int stage_mode(const agile_dev_table_t &T, bool want_ranges, bool want_compact = false,
                       bool want_bits = false) {
     if (T.npages == 0) return STAGE_NONE;
-    if (want_compact && T.crange != nullptr && stage_bytes(T, STAGE_COMPACT) <= 96 * 1024)
-        return STAGE_COMPACT;
     const int b = want_bits ? ST_BITS : 0;
+    if (want_compact && T.crange != nullptr) {
+        if (b && stage_bytes(T, STAGE_COMPACT | b) <= 104 * 1024) return STAGE_COMPACT | b;
+        if (stage_bytes(T, STAGE_COMPACT) <= 96 * 1024) return STAGE_COMPACT;
+    }
     if (want_ranges && stage_bytes(T, STAGE_ALL | b) <= 96 * 1024) return STAGE_ALL | b;
     if (stage_bytes(T, STAGE_PAGES | b) <= (want_bits ? 96 : 48) * 1024) return STAGE_PAGES | b;
     if (want_bits && stage_bytes(T, STAGE_BITS) <= 48 * 1024) return STAGE_BITS;
