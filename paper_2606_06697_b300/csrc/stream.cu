@@ -14,55 +14,51 @@ using agile::WarpSlots;
 
 constexpr int kThreads = 512;
 
-template <int OP, bool GUARD, int MODE, int POLICY>
-__global__ void __launch_bounds__(kThreads, 2)
+// Launch shape, measured on the 2^28-element arrays: the guarded kernels run one block of
+// 512 threads per SM, each lane keeping 8 units per array in flight (128 registers); the
+// unguarded twins run two blocks per SM with 4 units per lane, their best shape.
+template <bool GUARD> struct Shape;
+template <> struct Shape<true> { static constexpr int kUnits = 8, kBlocksPerSm = 1; };
+template <> struct Shape<false> { static constexpr int kUnits = 4, kBlocksPerSm = 2; };
+
+template <int OP, bool GUARD, int POLICY>
+__global__ void __launch_bounds__(kThreads, Shape<GUARD>::kBlocksPerSm)
 k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restrict__ b,
          const float *__restrict__ c, size_t n, float s, LogDev *log) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long s_bar;
+    constexpr int U = Shape<GUARD>::kUnits;
+    constexpr uint32_t kTile = 32 * U;
     __shared__ WarpSlots S;
     TView V{};
     if constexpr (GUARD) {
+        // The page map is read through L1 rather than staged: a warp checks three spans
+        // per tile, and skipping the staging lets every block start streaming at once.
         agile::slots_init(S);
         __syncthreads();
-        V = agile::stage_table<MODE>(T, smem, &s_bar, log);
+        V = agile::view_of(T);
     }
     const size_t n4 = n >> 2;
     const size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
-    const size_t tiles = (n4 + agile::kStreamTileUnits - 1) / agile::kStreamTileUnits;
+    const size_t tiles = (n4 + kTile - 1) / kTile;
     for (size_t t = warp; t < tiles; t += nwarps)             // warp-uniform
-        agile::stream_warp_tile<OP, GUARD, POLICY>(V, T, a, b, c, t, n4, n, s, S, true);
+        agile::stream_warp_tile<OP, GUARD, POLICY, U>(V, T, a, b, c, t, n4, n, s, S, true);
     // Elements past the last whole 16-byte unit: 4-byte accesses by the last warp.
     if ((n & 3) && blockIdx.x == gridDim.x - 1 && (threadIdx.x >> 5) == (blockDim.x >> 5) - 1)
         agile::stream_tail<OP, GUARD, POLICY>(V, T, a, b, c, n, s, S);
     if constexpr (GUARD) agile::slots_flush(log, S);
 }
 
-template <int OP, bool GUARD, int MODE, int POLICY>
+template <int OP, bool GUARD, int POLICY>
 int launch(const agile_dev_table_t &T, float *a, const float *b, const float *c, size_t n,
            float s, LogDev *log, cudaStream_t st) {
-    const uint32_t smem = GUARD ? agile::stage_bytes(T, MODE) : 0;
-    if (smem > 48 * 1024) {
-        AGILE_CUDA_TRY(cudaFuncSetAttribute(k_stream<OP, GUARD, MODE, POLICY>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    }
-    const size_t tiles = ((n >> 2) + agile::kStreamTileUnits - 1) / agile::kStreamTileUnits;
+    constexpr uint32_t kTile = 32 * Shape<GUARD>::kUnits;
+    const size_t tiles = ((n >> 2) + kTile - 1) / kTile;
     const size_t want = (tiles * 32 + kThreads - 1) / kThreads;
-    const size_t cap = (size_t)agile::sm_count() * 2;
+    const size_t cap = (size_t)agile::sm_count() * Shape<GUARD>::kBlocksPerSm;
     const unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
-    k_stream<OP, GUARD, MODE, POLICY><<<blocks, kThreads, smem, st>>>(T, a, b, c, n, s, log);
+    k_stream<OP, GUARD, POLICY><<<blocks, kThreads, 0, st>>>(T, a, b, c, n, s, log);
     AGILE_CUDA_TRY(cudaGetLastError());
     return AGILE_OK;
-}
-
-template <int OP, int POLICY>
-int by_mode(const agile_dev_table_t &T, float *a, const float *b, const float *c, size_t n,
-            float s, LogDev *log, cudaStream_t st) {
-    switch (agile::stage_mode(T, false)) {
-        case agile::STAGE_PAGES: return launch<OP, true, agile::STAGE_PAGES, POLICY>(T, a, b, c, n, s, log, st);
-        default: return launch<OP, true, agile::STAGE_NONE, POLICY>(T, a, b, c, n, s, log, st);
-    }
 }
 
 template <int OP>
@@ -70,12 +66,12 @@ int dispatch(const agile_dev_table_t *tbl, float *a, const float *b, const float
              float s, int policy, LogDev *log, cudaStream_t st) {
     if (tbl == nullptr) {
         agile_dev_table_t none = {};
-        return launch<OP, false, agile::STAGE_NONE, AGILE_POLICY_REPORT>(none, a, b, c, n, s, nullptr, st);
+        return launch<OP, false, AGILE_POLICY_REPORT>(none, a, b, c, n, s, nullptr, st);
     }
     switch (policy) {
-        case AGILE_POLICY_POISON: return by_mode<OP, AGILE_POLICY_POISON>(*tbl, a, b, c, n, s, log, st);
-        case AGILE_POLICY_SINK: return by_mode<OP, AGILE_POLICY_SINK>(*tbl, a, b, c, n, s, log, st);
-        case AGILE_POLICY_REPORT: return by_mode<OP, AGILE_POLICY_REPORT>(*tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_POISON: return launch<OP, true, AGILE_POLICY_POISON>(*tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_SINK: return launch<OP, true, AGILE_POLICY_SINK>(*tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_REPORT: return launch<OP, true, AGILE_POLICY_REPORT>(*tbl, a, b, c, n, s, log, st);
         default: return AGILE_ERR_INVALID_ARG;
     }
 }

@@ -1,8 +1,8 @@
 // Guarded streaming bodies shared by the standalone kernels and the batched persistent
 // kernel: COPY a = b, SCALE a = s*b, TRIAD a = b + s*c (one fused multiply-add).
 //
-// Work is cut into warp tiles of 128 16-byte units (2 KiB per array); lane l handles units
-// l, l+32, l+64, l+96, so every access is coalesced. Before a tile the warp checks each
+// Work is cut into warp tiles of 32*U 16-byte units (U = 4: 2 KiB per array); lane l
+// handles units l, l+32, ..., l+32(U-1), so every access is coalesced. Before a tile the warp checks each
 // array's 2 KiB span once (span_allowed: first and last byte in all-user pages of the
 // same allocation, else the span classified as one access). Only a tile whose spans are
 // not all allowed takes the per-access path (slow_tile, out of line), where each lane
@@ -16,7 +16,7 @@
 
 namespace agile {
 
-constexpr int kStreamU = 4;                         // units per lane per warp tile
+constexpr int kStreamU = 4;                         // default units per lane per warp tile
 constexpr uint32_t kStreamTileUnits = 32 * kStreamU;
 
 template <int OP>
@@ -43,10 +43,10 @@ __device__ __forceinline__ bool lane_ok(const TView &V, uint64_t a, uint32_t w, 
     return false;
 }
 
-// Per-access path for one warp tile (units u0 .. u0+127 clipped to n4; for the n mod 4
+// Per-access path for one warp tile (units u0 .. u0+32U-1 clipped to n4; for the n mod 4
 // tail, the lane's element is 4*n4 + lane with 4-byte accesses). Warp-collective.
 // Applies the policy and logs into the warp's slot.
-template <int OP, int POLICY, bool TAIL>
+template <int OP, int POLICY, bool TAIL, int U = kStreamU>
 static __device__ __noinline__ void slow_tile(const TView &V, const agile_dev_table_t &T, float *a,
                                        const float *b, const float *c, size_t u0, size_t n4,
                                        size_t n, float s, WarpSlots &S) {
@@ -61,7 +61,7 @@ static __device__ __noinline__ void slow_tile(const TView &V, const agile_dev_ta
         float4 *a4 = reinterpret_cast<float4 *>(a);
         const float4 *zero4 = reinterpret_cast<const float4 *>(T.zero_page);
 #pragma unroll 1
-        for (int k = 0; k < kStreamU; ++k) {
+        for (int k = 0; k < U; ++k) {
             const size_t u = u0 + 32 * k + lane;
             if (u >= n4) continue;
             const bool okb = lane_ok(V, (uint64_t)(b4 + u), 16, kSiteB, ll);
@@ -90,9 +90,9 @@ static __device__ __noinline__ void slow_tile(const TView &V, const agile_dev_ta
     warp_note(S, ll);
 }
 
-// One warp tile t (units t*128 .. t*128+127, clipped to n4): the span checks when
+// One warp tile t (units t*32U .. t*32U+32U-1, clipped to n4): the span checks when
 // `spans` is set, else straight to the per-access path. Warp-collective.
-template <int OP, bool GUARD, int POLICY>
+template <int OP, bool GUARD, int POLICY, int U = kStreamU>
 __device__ __forceinline__ void stream_warp_tile(const TView &V, const agile_dev_table_t &T,
                                                  float *a, const float *b, const float *c,
                                                  size_t t, size_t n4, size_t n, float s,
@@ -102,34 +102,35 @@ __device__ __forceinline__ void stream_warp_tile(const TView &V, const agile_dev
     const float4 *c4 = reinterpret_cast<const float4 *>(c);
     float4 *a4 = reinterpret_cast<float4 *>(a);
     const uint32_t lane = threadIdx.x & 31;
-    const size_t u0 = t * kStreamTileUnits;
-    bool fast = u0 + kStreamTileUnits <= n4;
+    constexpr uint32_t kTile = 32 * U;
+    const size_t u0 = t * kTile;
+    bool fast = u0 + kTile <= n4;
     if constexpr (GUARD) {
-        fast = fast && spans && span_allowed(V, (uint64_t)(b4 + u0), 16 * kStreamTileUnits) &&
-               span_allowed(V, (uint64_t)(a4 + u0), 16 * kStreamTileUnits);
+        fast = fast && spans && span_allowed(V, (uint64_t)(b4 + u0), 16 * kTile) &&
+               span_allowed(V, (uint64_t)(a4 + u0), 16 * kTile);
         if constexpr (kTriad)
-            fast = fast && span_allowed(V, (uint64_t)(c4 + u0), 16 * kStreamTileUnits);
+            fast = fast && span_allowed(V, (uint64_t)(c4 + u0), 16 * kTile);
         if (!fast) {
-            slow_tile<OP, POLICY, false>(V, T, a, b, c, u0, n4, n, s, S);
+            slow_tile<OP, POLICY, false, U>(V, T, a, b, c, u0, n4, n, s, S);
             return;
         }
     } else if (!fast) {                               // unguarded partial tile
 #pragma unroll
-        for (int k = 0; k < kStreamU; ++k) {
+        for (int k = 0; k < U; ++k) {
             const size_t u = u0 + 32 * k + lane;
             if (u < n4) __stcs(a4 + u, op4<OP>(s, __ldcs(b4 + u), kTriad ? __ldcs(c4 + u) : float4{}));
         }
         return;
     }
-    float4 vb[kStreamU], vc[kStreamU];
+    float4 vb[U], vc[U];
 #pragma unroll
-    for (int k = 0; k < kStreamU; ++k) {
+    for (int k = 0; k < U; ++k) {
         vb[k] = __ldcs(b4 + u0 + 32 * k + lane);
         if constexpr (kTriad) vc[k] = __ldcs(c4 + u0 + 32 * k + lane);
         else vc[k] = vb[k];
     }
 #pragma unroll
-    for (int k = 0; k < kStreamU; ++k) __stcs(a4 + u0 + 32 * k + lane, op4<OP>(s, vb[k], vc[k]));
+    for (int k = 0; k < U; ++k) __stcs(a4 + u0 + 32 * k + lane, op4<OP>(s, vb[k], vc[k]));
 }
 
 // The n mod 4 tail elements (4-byte accesses), by one warp.
