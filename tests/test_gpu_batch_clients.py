@@ -29,11 +29,14 @@ def same(a, b):
         (lb.count, lb.key, lb.addr, lb.width, lb.verdict, lb.site, lb.range_id, lb.client)
 
 
-def oracle_outputs(cs):
-    """The oracle's output and log for every client, from the device inputs."""
+def oracle_outputs(cs, which=None):
+    """The oracle's output and log for every client (or the clients `which`), from the
+    device inputs."""
     res = []
     host = cs.arena.cpu().numpy()
     for i, c in enumerate(cs.clients):
+        if which is not None and i not in which:
+            continue
         s, n, b = c["spec"], c["n"], c["buf"]
         off, span = c["arena_off"], c["span"]
         if s["op"] == "copy":
