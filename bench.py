@@ -296,10 +296,11 @@ def run_ours(args, ws, rank, local):
         kern_u, value_u = {op: None for op in ops}, None
 
     # the same kernels from hand-written PTX through the guard pass (poison)
-    ptx_kern, ptx_gbs, ptx_plain_gbs = None, None, None
+    ptx_kern, ptx_gbs, ptx_plain_gbs, ptx_ap_gbs = None, None, None, None
     if "ptx" in args.legs:
         ptx_kern = ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C)
         ptx_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("guarded")) / 1e3) / 1e9
+        ptx_ap_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("aperture")) / 1e3) / 1e9
         ptx_plain_gbs = STEP_BYTES / (sum(v for k, v in ptx_kern.items() if k.endswith("plain")) / 1e3) / 1e9
 
     # dominant kernel roofline
@@ -343,6 +344,7 @@ def run_ours(args, ws, rank, local):
             "guarded_over_unguarded": value / ws / value_u if value_u else None,
             "ptx_injected_gbs": ptx_gbs, "ptx_plain_gbs": ptx_plain_gbs,
             "ptx_injected_over_plain": ptx_gbs / ptx_plain_gbs if ptx_gbs else None,
+            "ptx_aperture_rule_gbs": ptx_ap_gbs,
             "ptx_kernel_ms": ptx_kern,
             "kernel_ms": {f"{op}_guarded": kern[op] for op in ops} |
                          {f"{op}_unguarded": kern_u[op] for op in ops},
@@ -391,14 +393,18 @@ def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):
     import ctypes
     src = open(PTX_STREAM).read()
     guarded = ag.agile_module_load(ag.agile_guard_instrument_ptx(src, "poison")[0])
+    ap = syn.table1_protected()
+    aperture = ag.agile_module_load(ag.agile_guard_instrument_ptx(
+        src, "poison", apertures=(ap.base, ap.size, ap.kind, ap.ident))[0])
     plain = ag.agile_module_load(src)
     ag.agile_violation_log_init(log, 0, stream)
     ag.agile_module_bind(guarded, dtab, log, stream)
+    ag.agile_module_bind(aperture, None, log, stream)
     grid = torch.cuda.get_device_properties(dev).multi_processor_count * 4
     args = [ctypes.c_uint64(A.data_ptr()), ctypes.c_uint64(B.data_ptr()),
             ctypes.c_uint64(C.data_ptr()), ctypes.c_uint64(N_ELEMS), ctypes.c_float(3.0)]
     out = {}
-    for name, mod in (("guarded", guarded), ("plain", plain)):
+    for name, mod in (("guarded", guarded), ("aperture", aperture), ("plain", plain)):
         for op in ("copy", "scale", "triad"):
             for _ in range(3):
                 ag.agile_module_launch(mod, f"agile_ptx_{op}", grid, 512, args, stream)
@@ -415,6 +421,7 @@ def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):
     rc, rec = ag.agile_violation_log_read(log, stream)
     assert rc == 0 and rec.count == 0, "violation in the PTX-injected run"
     guarded.unload()
+    aperture.unload()
     plain.unload()
     return out
 

@@ -453,6 +453,10 @@ typedef struct {
     int policy;                    /* AGILE_POLICY_*                                     */
     const char *const *skip;       /* functions left unguarded (trusted module bodies,   */
     size_t nskip;                  /*   Sec. V-E); may be NULL                            */
+    const agile_range_t *apertures; /* with napertures > 0: the aperture rule (Table I;   */
+    size_t napertures;             /*   rules as agile_aperture_check_batch) compiled into
+                                         the module as constants, in place of the table;
+                                         REMAP_OR is then refused                        */
 } agile_instrument_opts_t;
 
 typedef struct {
@@ -480,7 +484,8 @@ AGILE_API int agile_module_load(const char *ptx, agile_module_t **out);
 
 /* Point the module's guard globals at an uploaded table's device buffer and a log
  * (d_log may be NULL: violations then go unrecorded). Synchronous. INVALID_ARG for a
- * module that was not instrumented. */
+ * module that was not instrumented, or for tbl == NULL unless the module was
+ * instrumented with apertures (it then needs only the log). */
 AGILE_API int agile_module_bind(agile_module_t *m, const agile_dev_table_t *tbl, void *d_log, void *stream);
 
 /* Launch kernel `name` of the module: grid and block sizes, `args` = array of

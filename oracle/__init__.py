@@ -23,6 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 VERDICT_NAMES = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID", "NOT_EXACT"]
 NO_RANGE = 0xFFFFFFFF
 POLICY = {"poison": 0, "sink": 1, "report": 2, "remap": 4}
+RULES = {"table": 0, "aperture": 1}
 STREAM_OPS = {"copy": 0, "scale": 1, "triad": 2}
 
 
@@ -155,9 +156,10 @@ def validate_exact(r, ptr: np.ndarray, nbytes: np.ndarray):
 
 
 def stream(op: str, r, va: dict, b: np.ndarray, c: np.ndarray | None, a0: np.ndarray,
-           s: float = 3.0, policy: str = "poison"):
+           s: float = 3.0, policy: str = "poison", rule: str = "table"):
     """Guarded copy / scale / triad (Sec. V-E guard and policies; access order stated in
-    agile_oracle.c). va: {'a','b','c'} -> guarded-space addresses. Returns (a, log)."""
+    agile_oracle.c). va: {'a','b','c'} -> guarded-space addresses. rule 'aperture' checks
+    against the ranges r as apertures (Table I rule). Returns (a, log)."""
     base, size, kind, ident = _table(r)
     n = len(b)
     b = np.ascontiguousarray(b, dtype=np.float32)
@@ -167,6 +169,7 @@ def stream(op: str, r, va: dict, b: np.ndarray, c: np.ndarray | None, a0: np.nda
     _L().orc_stream(ctypes.c_int(STREAM_OPS[op]), ctypes.c_size_t(n), ctypes.c_uint64(va["a"]),
                     ctypes.c_uint64(va["b"]), ctypes.c_uint64(va.get("c", 0)), ctypes.c_float(s),
                     _p(b), _p(c), _p(a), ctypes.c_int(POLICY[policy]),
+                    ctypes.c_int(RULES[rule]),
                     ctypes.c_size_t(len(base)), _p(base), _p(size), _p(kind), _p(ident),
                     ctypes.byref(log))
     return a, Log._of(log)
@@ -187,7 +190,7 @@ IRREGULAR = {"gather": 0, "scatter": 1, "hist": 2}
 
 
 def irregular(kind: str, r, arena: np.ndarray, arena_va: int, va: dict, n: int,
-              policy: str = "poison", remap: int = 0):
+              policy: str = "poison", remap: int = 0, rule: str = "table"):
     """Guarded gather / scatter / histogram over an arena copy (Sec. V-E guard and
     policies; access order stated in agile_oracle.c). `arena` (uint8) is updated in
     place; va: {'idx', 't', 'out'} guarded-space addresses; remap is the REMAP_OR mask.
@@ -200,7 +203,8 @@ def irregular(kind: str, r, arena: np.ndarray, arena_va: int, va: dict, n: int,
     rc = f(ctypes.c_int(IRREGULAR[kind]), ctypes.c_size_t(n), ctypes.c_uint64(arena_va),
            _p(arena), ctypes.c_size_t(len(arena)), ctypes.c_uint64(va["idx"]),
            ctypes.c_uint64(va["t"]), ctypes.c_uint64(va.get("out", 0)),
-           ctypes.c_int(POLICY[policy]), ctypes.c_uint64(remap), ctypes.c_size_t(len(base)),
+           ctypes.c_int(POLICY[policy]), ctypes.c_uint64(remap), ctypes.c_int(RULES[rule]),
+           ctypes.c_size_t(len(base)),
            _p(base), _p(size), _p(kind_), _p(ident), ctypes.byref(log))
     if rc != 0:
         raise ValueError("an access that is carried out falls outside the arena")

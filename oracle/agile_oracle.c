@@ -299,6 +299,29 @@ void orc_validate_exact(size_t n, const uint64_t *base, const uint64_t *size, co
     }
 }
 
+/* The rule a guarded kernel applies: the table rule (classify_sorted over the table) or
+ * the aperture rule (classify_aperture over the apertures, Table I / Sec. V-E). */
+typedef struct {
+    orc_table t;
+    orc_sorted *s;          /* NULL under the aperture rule */
+} orc_rule;
+
+static orc_rule rule_new(int aperture, size_t tn, const uint64_t *base, const uint64_t *size,
+                         const uint32_t *kind, const uint32_t *id) {
+    orc_rule r;
+    r.t.n = tn; r.t.base = base; r.t.size = size; r.t.kind = kind; r.t.id = id;
+    r.s = aperture ? NULL : sorted_new(&r.t);
+    return r;
+}
+
+static uint32_t rule_classify(const orc_rule *r, uint64_t a, uint64_t w, uint32_t *rid) {
+    return r->s ? classify_sorted(r->s, a, w, rid) : classify_aperture(&r->t, a, w, rid);
+}
+
+static void rule_free(orc_rule *r) {
+    if (r->s) sorted_free(r->s);
+}
+
 /*
  * Guarded streaming kernels: copy a = b, scale a = s*b, triad a = b + s*c (one fused
  * multiply-add, rounded once). Each is a sequence of accesses in this order per unit:
@@ -310,13 +333,13 @@ void orc_validate_exact(size_t n, const uint64_t *base, const uint64_t *size, co
  * Policy (Sec. V-E): poison -- a denied load reads 0, a denied store is dropped, each is
  * logged; sink -- the same observable data (loads read a zero page, stores land in a
  * write sink), logged; report -- the access proceeds, logged.
+ * aperture: 0 checks against the table, 1 against the apertures (the ranges passed).
  */
 void orc_stream(int op, size_t n, uint64_t va_a, uint64_t va_b, uint64_t va_c, float s,
-                const float *b, const float *c, float *a, int policy, size_t tn,
+                const float *b, const float *c, float *a, int policy, int aperture, size_t tn,
                 const uint64_t *base, const uint64_t *size, const uint32_t *kind,
                 const uint32_t *id, orc_log *log) {
-    orc_table t = {tn, base, size, kind, id};
-    orc_sorted *srt = sorted_new(&t);
+    orc_rule R = rule_new(aperture, tn, base, size, kind, id);
     log_clear(log);
     size_t units = n / 4;
     size_t total = units + (n - units * 4);
@@ -328,21 +351,21 @@ void orc_stream(int op, size_t n, uint64_t va_a, uint64_t va_b, uint64_t va_c, f
         uint64_t w = 4 * cnt, off = 4 * e0;
         float vb[4] = {0, 0, 0, 0}, vc[4] = {0, 0, 0, 0}, out[4];
         uint32_t rid, v;
-        v = classify_sorted(srt, va_b + off, w, &rid);
+        v = rule_classify(&R, va_b + off, w, &rid);
         if (v == V_ALLOW || policy == P_REPORT) memcpy(vb, b + e0, 4 * cnt);
         if (v != V_ALLOW) log_note(log, va_b + off, va_b + off, (uint32_t)w, v, 0, rid);
         if (op == 2) {
-            v = classify_sorted(srt, va_c + off, w, &rid);
+            v = rule_classify(&R, va_c + off, w, &rid);
             if (v == V_ALLOW || policy == P_REPORT) memcpy(vc, c + e0, 4 * cnt);
             if (v != V_ALLOW) log_note(log, va_c + off, va_c + off, (uint32_t)w, v, 1, rid);
         }
         for (size_t k = 0; k < cnt; ++k)
             out[k] = op == 0 ? vb[k] : op == 1 ? s * vb[k] : fmaf(s, vc[k], vb[k]);
-        v = classify_sorted(srt, va_a + off, w, &rid);
+        v = rule_classify(&R, va_a + off, w, &rid);
         if (v == V_ALLOW || policy == P_REPORT) memcpy(a + e0, out, 4 * cnt);
         if (v != V_ALLOW) log_note(log, va_a + off, va_a + off, (uint32_t)w, v, store_site, rid);
     }
-    sorted_free(srt);
+    rule_free(&R);
 }
 
 /* Unguarded reference kernels: the same arithmetic with no table. */
@@ -380,26 +403,25 @@ static int in_arena(const orc_arena *A, uint64_t a, uint64_t w) {
  * which address. REMAP (Sec. V-E remap_or, with the paper's caveat that the target must
  * itself be a live user allocation): a denied access moves to a | remap when that access is
  * allowed, else it is dropped as under poison. */
-static int guarded(const orc_sorted *s, orc_log *log, int policy, uint64_t remap, uint64_t a,
+static int guarded(const orc_rule *R, orc_log *log, int policy, uint64_t remap, uint64_t a,
                    uint64_t w, uint32_t site, uint64_t *at) {
-    uint32_t rid, v = classify_sorted(s, a, w, &rid);
+    uint32_t rid, v = rule_classify(R, a, w, &rid);
     *at = a;
     if (v == V_ALLOW) return 1;
     log_note(log, a, a, (uint32_t)w, v, site, rid);
     if (policy == P_REPORT) return 1;
     if (policy == P_REMAP) {
         uint32_t r2;
-        if (classify_sorted(s, a | remap, w, &r2) == V_ALLOW) { *at = a | remap; return 1; }
+        if (rule_classify(R, a | remap, w, &r2) == V_ALLOW) { *at = a | remap; return 1; }
     }
     return 0;
 }
 
 int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t arena_len,
                   uint64_t va_idx, uint64_t va_t, uint64_t va_out, int policy, uint64_t remap,
-                  size_t tn, const uint64_t *base, const uint64_t *size, const uint32_t *kindv,
-                  const uint32_t *id, orc_log *log) {
-    orc_table t = {tn, base, size, kindv, id};
-    orc_sorted *s = sorted_new(&t);
+                  int aperture, size_t tn, const uint64_t *base, const uint64_t *size,
+                  const uint32_t *kindv, const uint32_t *id, orc_log *log) {
+    orc_rule R = rule_new(aperture, tn, base, size, kindv, id);
     orc_arena A = {arena_va, arena, arena_len};
     int rc = 0;
     log_clear(log);
@@ -411,7 +433,7 @@ int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t 
         /* index loads */
         for (size_t h = 0; h < (vec ? 2u : 1u); ++h) {
             uint64_t a = va_idx + 8 * e0 + 16 * h, w = vec ? 16 : 8, at;
-            if (guarded(s, log, policy, remap, a, w, (uint32_t)h, &at)) {
+            if (guarded(&R, log, policy, remap, a, w, (uint32_t)h, &at)) {
                 if (!in_arena(&A, at, w)) { rc = -1; break; }
                 memcpy(idx + 2 * h, arena + (at - A.va), w);
             }
@@ -420,7 +442,7 @@ int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t 
         float out[4] = {0, 0, 0, 0};
         for (size_t k = 0; k < cnt && rc == 0; ++k) {
             uint64_t a = va_t + 4 * (uint64_t)idx[k], at;
-            if (!guarded(s, log, policy, remap, a, 4, 2, &at)) continue;
+            if (!guarded(&R, log, policy, remap, a, 4, 2, &at)) continue;
             if (!in_arena(&A, at, 4)) { rc = -1; break; }
             uint8_t *p = arena + (at - A.va);
             if (kind == IR_GATHER) {
@@ -438,12 +460,12 @@ int orc_irregular(int kind, size_t n, uint64_t arena_va, uint8_t *arena, size_t 
         /* gather's output store */
         if (kind == IR_GATHER && rc == 0) {
             uint64_t a = va_out + 4 * e0, w = 4 * cnt, at;
-            if (guarded(s, log, policy, remap, a, w, 3, &at)) {
+            if (guarded(&R, log, policy, remap, a, w, 3, &at)) {
                 if (!in_arena(&A, at, w)) rc = -1;
                 else memcpy(arena + (at - A.va), out, w);
             }
         }
     }
-    sorted_free(s);
+    rule_free(&R);
     return rc;
 }

@@ -97,7 +97,8 @@ class WorkerConfig(ctypes.Structure):
 
 class _InstrOpts(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int), ("skip", ctypes.POINTER(ctypes.c_char_p)),
-                ("nskip", ctypes.c_size_t)]
+                ("nskip", ctypes.c_size_t), ("apertures", ctypes.c_void_p),
+                ("napertures", ctypes.c_size_t)]
 
 
 class _InstrReport(ctypes.Structure):
@@ -529,12 +530,15 @@ def agile_worker_device_bytes(cfg: WorkerConfig) -> int:
 # ---------------------------------------------------------------- PTX guard pass
 
 
-def agile_guard_instrument_ptx(ptx: str, policy: str = "poison", skip=()):
-    """Returns (instrumented PTX text, report dict)."""
+def agile_guard_instrument_ptx(ptx: str, policy: str = "poison", skip=(), apertures=None):
+    """Returns (instrumented PTX text, report dict). apertures: (base, size, kind, ident)
+    parallel arrays selecting the aperture rule, or None for the table rule."""
     names = [s.encode() for s in skip]
     arr = (ctypes.c_char_p * max(len(names), 1))(*names) if names else None
+    ap_arr, n_ap = _range_array(*apertures) if apertures is not None else (None, 0)
     opts = _InstrOpts(POLICIES[policy], ctypes.cast(arr, ctypes.POINTER(ctypes.c_char_p))
-                      if arr is not None else None, len(names))
+                      if arr is not None else None, len(names),
+                      ctypes.cast(ap_arr, ctypes.c_void_p) if n_ap else None, n_ap)
     out = ctypes.c_void_p()
     out_len = ctypes.c_size_t()
     rep = _InstrReport()
@@ -581,9 +585,10 @@ def agile_module_load(ptx: str) -> Module:
     return Module(out.value)
 
 
-def agile_module_bind(m: Module, dev: DevTable, d_log=None, stream=None) -> None:
-    _check(lib().agile_module_bind(m.handle, dev.ref, _dptr(d_log), _stream(stream)),
-           "agile_module_bind")
+def agile_module_bind(m: Module, dev: DevTable | None, d_log=None, stream=None) -> None:
+    """dev may be None for a module instrumented with apertures."""
+    _check(lib().agile_module_bind(m.handle, dev.ref if dev is not None else None, _dptr(d_log),
+                                   _stream(stream)), "agile_module_bind")
 
 
 def agile_module_launch(m: Module, name: str, grid: int, block: int, args, stream=None) -> None:

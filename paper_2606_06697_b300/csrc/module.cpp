@@ -13,6 +13,7 @@
 struct agile_module {
     cudaLibrary_t lib = nullptr;
     bool guarded = false;   // carries the guard's module globals
+    bool aperture = false;  // guarded by the aperture rule: needs no table
     bool bound = false;
 };
 
@@ -38,12 +39,15 @@ int agile_module_load(const char *ptx, agile_module_t **out) {
     size_t b = 0;
     m->guarded = cudaLibraryGetGlobal(&g, &b, m->lib, "__agile_guard_table") == cudaSuccess;
     (void)cudaGetLastError();
+    m->aperture = m->guarded &&
+                  cudaLibraryGetGlobal(&g, &b, m->lib, "__agile_aperture_mode") == cudaSuccess;
+    (void)cudaGetLastError();
     *out = m;
     return AGILE_OK;
 }
 
 int agile_module_bind(agile_module_t *m, const agile_dev_table_t *tbl, void *d_log, void *stream) {
-    if (m == nullptr || tbl == nullptr || !m->guarded) return AGILE_ERR_INVALID_ARG;
+    if (m == nullptr || !m->guarded || (tbl == nullptr && !m->aperture)) return AGILE_ERR_INVALID_ARG;
     if (d_log != nullptr && ((uintptr_t)d_log & 15) != 0) return AGILE_ERR_ALIGN;
     void *g_tbl = nullptr, *g_log = nullptr;
     size_t b1 = 0, b2 = 0;
@@ -51,7 +55,7 @@ int agile_module_bind(agile_module_t *m, const agile_dev_table_t *tbl, void *d_l
     AGILE_CUDA_TRY(cudaLibraryGetGlobal(&g_log, &b2, m->lib, "__agile_guard_log"));
     if (b1 != 8 || b2 != 8) return AGILE_ERR_PTX_UNSUPPORTED;
     // The header sits at the start of the table's device buffer.
-    uint64_t vals[2] = {(uint64_t)(uintptr_t)tbl->page - 256, (uint64_t)(uintptr_t)d_log};
+    uint64_t vals[2] = {tbl ? (uint64_t)(uintptr_t)tbl->page - 256 : 0, (uint64_t)(uintptr_t)d_log};
     cudaStream_t st = (cudaStream_t)stream;
     AGILE_CUDA_TRY(cudaMemcpyAsync(g_tbl, &vals[0], 8, cudaMemcpyHostToDevice, st));
     AGILE_CUDA_TRY(cudaMemcpyAsync(g_log, &vals[1], 8, cudaMemcpyHostToDevice, st));

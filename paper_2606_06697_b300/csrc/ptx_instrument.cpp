@@ -17,6 +17,8 @@
 //   sink page; REPORT changes nothing; TRAP emits `@!ok trap;`.
 // The table's device address is read once per function from the module global
 // __agile_guard_table; site = the access's position in its function.
+#include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <set>
@@ -100,9 +102,33 @@ struct Access {
     std::string dest;
 };
 
+// One aperture in decision order (MMIO before protected, then by base).
+struct Aperture {
+    uint64_t lo, end;
+    uint32_t verdict, id;
+};
+
 class Rewriter {
   public:
-    Rewriter(int policy, const std::set<std::string> &skip) : policy_(policy), skip_(skip) {}
+    Rewriter(int policy, const std::set<std::string> &skip, std::vector<Aperture> aps, bool aperture)
+        : policy_(policy), skip_(skip), aps_(std::move(aps)), aperture_(aperture) {
+        if (aperture_ && !aps_.empty()) {
+            hull_lo_ = aps_[0].lo;
+            hull_end_ = aps_[0].end;
+            for (const Aperture &a : aps_) {
+                hull_lo_ = std::min(hull_lo_, a.lo);
+                hull_end_ = std::max(hull_end_, a.end);
+            }
+        }
+        injected_ = std::string(kGuardGlobalsPtx);
+        if (aperture_) {
+            injected_ += kApertureGlobalsPtx;
+            injected_ += ".global .align 4 .u32 __agile_aperture_mode = 1;\n";
+        }
+        injected_ += kGuardCheckHeadPtx;
+        injected_ += aperture_ ? aperture_body() : std::string(kGuardCheckTablePtx);
+        injected_ += kGuardCheckTailPtx;
+    }
 
     std::string run(const std::string &ptx) {
         if (ptx.find("__ag") != std::string::npos) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
@@ -125,7 +151,7 @@ class Rewriter {
             if (!injected && i >= inject_at) {
                 out.append(ptx, stmt_start, i - stmt_start);
                 out += "\n";
-                out += kGuardCheckPtx;
+                out += injected_;
                 stmt_start = i;
                 injected = true;
             }
@@ -157,7 +183,7 @@ class Rewriter {
             }
         }
         out.append(ptx, stmt_start, n - stmt_start);
-        if (!injected) out += kGuardCheckPtx;
+        if (!injected) out += injected_;
         // Fail closed: every memory-access opcode word of the input must have been seen
         // by the statement parser (guarded, skipped, or on a non-global space).
         if (count_access_words(clean) != rep_.guarded + rep_.skipped + other_space_)
@@ -193,7 +219,43 @@ class Rewriter {
 
     int policy_;
     const std::set<std::string> &skip_;
+    std::vector<Aperture> aps_;
+    bool aperture_;
+    uint64_t hull_lo_ = 0, hull_end_ = 0;   // smallest interval holding every aperture
+    std::string injected_;
     int label_ = 0;
+
+    static std::string hex(uint64_t v) {
+        char b[24];
+        std::snprintf(b, sizeof b, "0x%llx", (unsigned long long)v);
+        return b;
+    }
+
+    // Classification under the aperture rule, the apertures as constants: INVALID as in
+    // the table rule, else the first aperture (in decision order) the access overlaps.
+    std::string aperture_body() const {
+        std::string g =
+            "    mov.u32 %s2, 5;\n"
+            "    mov.u32 %s3, 0xFFFFFFFF;\n"
+            "    mov.b64 %t3, 0xFFFFFFFFFFFFFFFF;\n"
+            "    sub.s64 %t3, %t3, %t1;\n"
+            "    setp.gt.u64 %q0, %t0, %t3;\n"
+            "    setp.eq.u32 %q1, %s0, 0;\n"
+            "    or.pred %q0, %q0, %q1;\n"
+            "    @%q0 bra $AGC_LOG;\n"
+            "    add.s64 %t4, %t0, %t1;\n"
+            "    mov.u32 %s2, 0;\n";
+        for (size_t k = aps_.size(); k-- > 0;) {     // the lowest index overlapped wins
+            const Aperture &a = aps_[k];
+            g += "    setp.lt.u64 %q1, %t0, " + hex(a.end) + ";\n"
+                 "    setp.gt.and.u64 %q1, %t4, " + hex(a.lo) + ", %q1;\n"
+                 "    selp.u32 %s2, " + std::to_string(a.verdict) + ", %s2, %q1;\n"
+                 "    selp.u32 %s3, " + std::to_string(a.id) + ", %s3, %q1;\n";
+        }
+        g += "    setp.eq.u32 %q2, %s2, 0;\n"
+             "    @%q2 bra $AGC_RET;\n";
+        return g;
+    }
 
     static size_t match_brace(const std::string &clean, size_t open) {
         int depth = 0;
@@ -242,6 +304,11 @@ class Rewriter {
     }
 
     std::string prologue() const {
+        if (aperture_)
+            return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b64 %__agd<8>;\n"
+                   "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
+                   "\tmov.u64 %__agT3, __agile_zero_page;\n"
+                   "\tmov.u64 %__agT4, __agile_sink_page;\n";
         return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<8>;\n"
                "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
                "\tld.global.u64 %__agT7, [__agile_guard_table];\n"
@@ -486,7 +553,15 @@ class Rewriter {
     void emit_check(std::string &g, const Access &acc, const std::string &pred, bool neg, int site) {
         const std::string W = std::to_string(acc.width);
         const std::string L = "$__AG_OK_" + std::to_string(label_++);
-        g += "\tsub.s64 %__agd1, %__agd0, %__agT0;\n"
+        if (aperture_) {
+            // clear of the apertures' hull, and a + w does not wrap
+            g += "\tadd.s64 %__agd1, %__agd0, " + W + ";\n"
+                 "\tsetp.ge.u64 %__agp1, %__agd0, " + hex(hull_end_) + ";\n"
+                 "\tsetp.le.u64 %__agp0, %__agd1, " + hex(hull_lo_) + ";\n"
+                 "\tor.pred %__agp1, %__agp1, %__agp0;\n"
+                 "\tsetp.ge.u64 %__agp0, %__agd1, %__agd0;\n"
+                 "\tand.pred %__agp1, %__agp1, %__agp0;\n";
+        } else g += "\tsub.s64 %__agd1, %__agd0, %__agT0;\n"
              "\tshr.u64 %__agd2, %__agd1, %__agTlg;\n"
              "\tsetp.lt.u64 %__agp0, %__agd2, %__agT1;\n"
              "\tmov.b32 %__agr0, 0;\n"
@@ -532,6 +607,27 @@ extern "C" int agile_guard_instrument_ptx(const char *ptx, size_t len,
     *out_len = 0;
     int policy = opts ? opts->policy : AGILE_POLICY_POISON;
     if (policy < AGILE_POLICY_POISON || policy > AGILE_POLICY_REMAP_OR) return AGILE_ERR_INVALID_ARG;
+    std::vector<Aperture> aps;
+    const bool aperture = opts && opts->napertures > 0;
+    if (aperture) {
+        if (opts->napertures > AGILE_MAX_APERTURES) return AGILE_ERR_TOO_LARGE;
+        if (opts->apertures == nullptr || policy == AGILE_POLICY_REMAP_OR) return AGILE_ERR_INVALID_ARG;
+        std::vector<agile_range_t> r(opts->apertures, opts->apertures + opts->napertures);
+        for (const agile_range_t &x : r) {
+            if (x.kind != AGILE_PROTECTED && x.kind != AGILE_MMIO) return AGILE_ERR_BAD_KIND;
+            if (x.size == 0) return AGILE_ERR_ZERO_SIZE;
+            if (x.base > ~0ull - x.size) return AGILE_ERR_RANGE_OVERFLOW;
+        }
+        std::sort(r.begin(), r.end(), [](const agile_range_t &x, const agile_range_t &y) { return x.base < y.base; });
+        for (size_t k = 1; k < r.size(); ++k)
+            if (r[k].base < r[k - 1].base + r[k - 1].size) return AGILE_ERR_OVERLAP;
+        std::stable_sort(r.begin(), r.end(), [](const agile_range_t &x, const agile_range_t &y) {
+            return (x.kind == AGILE_MMIO) > (y.kind == AGILE_MMIO);
+        });
+        for (const agile_range_t &x : r)
+            aps.push_back({x.base, x.base + x.size,
+                           x.kind == AGILE_MMIO ? (uint32_t)AGILE_DENY_MMIO : (uint32_t)AGILE_DENY_PROTECTED, x.id});
+    }
     std::set<std::string> skip;
     if (opts && opts->nskip) {
         if (opts->skip == nullptr) return AGILE_ERR_INVALID_ARG;
@@ -539,7 +635,7 @@ extern "C" int agile_guard_instrument_ptx(const char *ptx, size_t len,
             if (opts->skip[i]) skip.insert(opts->skip[i]);
     }
     try {
-        Rewriter rw(policy, skip);
+        Rewriter rw(policy, skip, aps, aperture);
         std::string text = rw.run(std::string(ptx, len));
         char *buf = (char *)std::malloc(text.size() + 1);
         if (buf == nullptr) return AGILE_ERR_NOMEM;

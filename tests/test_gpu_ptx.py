@@ -161,3 +161,95 @@ def test_ptx_irregular_remap_parity(n):
                 assert IRR_SITES[kind][rec.site] == olog.site
     finally:
         mod.unload()
+
+
+# ---------------------------------------------------------------- aperture rule
+
+
+def _aps(r):
+    return (r.base, r.size, r.kind, r.ident)
+
+
+@pytest.mark.parametrize("policy", ["poison", "sink", "report"])
+def test_ptx_aperture_stream(policy):
+    """The pass with apertures (no table bound): a protected and an MMIO window over b and
+    c and a protected window over a; the straddling tail of a and the hole in c, which the
+    table rule denies, pass."""
+    n = 4099
+    _, _, nbytes = _hostile_layout(n, 0)
+    arena = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+    base = arena.data_ptr()
+    r, va, _ = _hostile_layout(n, base)
+    keep = r.kind != syn.KIND_USER
+    ap = syn._ranges(list(r.base[keep]) + [va["a"] + 4096], list(r.size[keep]) + [256],
+                     list(r.kind[keep]) + [syn.KIND_PROTECTED], list(r.ident[keep]) + [8])
+    mod = ag.agile_module_load(ag.agile_guard_instrument_ptx(STREAM, policy, apertures=_aps(ap))[0])
+    try:
+        b, c = _fill(n, 78)
+        A, B, C = (arena[va[k] - base:va[k] - base + 4 * n].view(torch.float32) for k in "abc")
+        B.copy_(torch.from_numpy(b))
+        C.copy_(torch.from_numpy(c))
+        for op in ("copy", "scale", "triad"):
+            a0 = np.full(n, -5.0, np.float32)
+            A.copy_(torch.from_numpy(a0))
+            log = new_log(client=11)
+            ag.agile_module_bind(mod, None, log)
+            launch(mod, op, A, B, C, n)
+            rc, rec = ag.agile_violation_log_read(log)
+            exp, olog = oracle.stream(op, ap, va, b, c if op == "triad" else None, a0, 3.0, policy,
+                                      rule="aperture")
+            assert (A.cpu().numpy().view(np.uint32) == exp.view(np.uint32)).all(), op
+            assert rc == 1 and rec.count == olog.count and rec.client == 11
+            assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
+                (olog.key, olog.addr, olog.width, olog.verdict, olog.range_id), (op, rec, olog)
+            assert SITE_MAP[op][rec.site] == olog.site
+    finally:
+        mod.unload()
+
+
+@pytest.mark.parametrize("policy", ["poison", "sink", "report"])
+@pytest.mark.parametrize("n", [7, 40_003])
+def test_ptx_aperture_irregular(policy, n):
+    """Irregular kernels under the aperture rule on the shadow/user layout, with extra
+    accesses into a hole (allowed by the aperture rule)."""
+    from test_gpu_irregular import put, remap_setup
+    half = 1 << 20
+    for kind in ("gather", "scatter", "hist"):
+        r, off, idx, key, cls, host, arena, base = remap_setup(n, half)
+        t = r.shifted(base)
+        keep = t.kind != syn.KIND_USER
+        ap = syn._ranges(t.base[keep], t.size[keep], t.kind[keep], t.ident[keep])
+        # the apertures are compiled into the module, so each arena gets its own
+        mod = ag.agile_module_load(ag.agile_guard_instrument_ptx(IRREGULAR, policy, apertures=_aps(ap))[0])
+        try:
+            ne = half // 4
+            hole = np.arange(0, n, 13)
+            idx, key = idx.copy(), key.copy()
+            idx[hole] = 2 * ne + hole % 4096            # the hole at [3 half, 4 half)
+            key[hole] = -2 * ne + hole % 4096
+            put(host, off["idx"], key if kind == "hist" else idx)
+            arena.copy_(torch.from_numpy(host))
+            log = new_log(client=12)
+            ag.agile_module_bind(mod, None, log)
+            target = off["bins"] if kind == "hist" else off["t"]
+            args = [ctypes.c_uint64(base + off["idx"]), ctypes.c_uint64(base + target),
+                    ctypes.c_uint64(base + off["out"]), ctypes.c_uint64(n)]
+            ag.agile_module_launch(mod, f"agile_ptx_{kind}", 148 * 2, 256, args)
+            rc, rec = ag.agile_violation_log_read(log)
+            va = {"t": base + target, "idx": base + off["idx"], "out": base + off["out"]}
+            olog = oracle.irregular(kind, ap, host, base, va, n, policy, rule="aperture")
+            assert (arena.cpu().numpy() == host).all(), kind
+            assert rec.count == olog.count and rec.client == 12
+            if olog.count:
+                assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
+                    (olog.key, olog.addr, olog.width, olog.verdict, olog.range_id), kind
+                assert IRR_SITES[kind][rec.site] == olog.site
+        finally:
+            mod.unload()
+
+
+def test_ptx_bind_without_table_only_for_aperture_modules():
+    m = ag.agile_module_load(ag.agile_guard_instrument_ptx(STREAM, "poison")[0])
+    with pytest.raises(ag.AgileError):
+        ag.agile_module_bind(m, None, new_log())
+    m.unload()

@@ -500,6 +500,36 @@ def test_remap_gather_moves_shadow_accesses_into_the_table():
     assert (a0 == a1).all() and l0 == l1
 
 
+def test_aperture_rule_in_kernels_sees_only_the_apertures():
+    """Under the aperture rule the gather's denials are exactly the accesses into the
+    protected apertures; an access into a hole, which the table rule denies, reads the
+    hole's contents."""
+    half = 1 << 20
+    t, arena, base, va, off, idx, key, cls = _remap_case(half=half)
+    n, ne = len(idx), half // 4
+    idx = idx.copy()
+    hole = np.arange(0, n, 97)
+    idx[hole] = 2 * ne + (np.arange(len(hole)) % 1000)   # [3 half, 3 half + 4000): a hole
+    cls = cls.copy()
+    cls[hole] = 3
+    arena[3 * half:3 * half + 4000] = (np.arange(4000) % 251 + 1).astype(np.uint8)
+    _put(arena, off["idx"], idx)
+    tv = arena[half:2 * half].view(np.float32)
+    hv = arena[3 * half:3 * half + 4000].view(np.float32)
+    keep = t.kind != syn.KIND_USER
+    ap = syn._ranges(t.base[keep], t.size[keep], t.kind[keep], t.ident[keep])
+    for rule, r in (("aperture", ap), ("table", t)):
+        a = arena.copy()
+        log = oracle.irregular("gather", r, a, base, va, n, "poison", rule=rule)
+        got = a[off["out"]:off["out"] + 4 * n].view(np.float32)
+        want = np.where(cls == 0, tv[np.clip(idx, 0, ne - 1)], np.float32(0))
+        if rule == "aperture":
+            want = np.where(cls == 3, hv[np.clip(idx - 2 * ne, 0, 999)], want)
+        assert (got == want).all(), rule
+        denied = (cls == 1) | (cls == 2) | ((cls == 3) & (rule == "table"))
+        assert log.count == int(denied.sum()), rule
+
+
 def test_remap_scatter_and_hist():
     half = 1 << 20
     t, arena, base, va, off, idx, key, cls = _remap_case(half=half)

@@ -87,6 +87,50 @@ def test_remap_policy_emission():
     assemble(out)
 
 
+def test_aperture_mode_emission():
+    """With apertures the pass compiles the aperture rule into the module: the inline test
+    is the apertures' hull (two compares and a wrap check, no table loads), the check
+    function compares against each aperture as a constant, and the module carries its own
+    zero and sink pages."""
+    import agile_synth as syn
+    ap = syn.table1_protected()
+    aps = (ap.base, ap.size, ap.kind, ap.ident)
+    out, rep = ag.agile_guard_instrument_ptx(STREAM, "poison", apertures=aps)
+    assert rep["guarded"] == 28
+    assert "__agile_aperture_mode = 1" in out and "__agile_zero_page[64]" in out
+    assert "[__agile_guard_table];" not in out.split(".entry", 1)[1]   # no table in the kernels
+    assert out.count("setp.ge.u64 %__agp1, %__agd0, 0xf8000000000;") == 28      # hull end
+    assert out.count("setp.le.u64 %__agp0, %__agd1, 0xf0000000000;") == 28      # hull start
+    assert "setp.lt.u64 %q1, %t0, 0xf1000000000;" in out                          # MMIO aperture
+    assert "selp.u32 %s2, 2, %s2, %q1;" in out and "selp.u32 %s2, 1, %s2, %q1;" in out
+    assemble(out)
+    for policy in ("sink", "report", "trap"):
+        assemble(ag.agile_guard_instrument_ptx(STREAM, policy, apertures=aps)[0])
+
+
+@pytest.mark.parametrize("bad,code", [
+    ("remap", -1),
+    ("sets", None),
+])
+def test_aperture_mode_refusals(bad, code):
+    import agile_synth as syn
+    ap = syn.table1_protected()
+    if bad == "remap":
+        with pytest.raises(ag.AgileError) as e:
+            ag.agile_guard_instrument_ptx(STREAM, "remap", apertures=(ap.base, ap.size, ap.kind, ap.ident))
+        assert e.value.code == code
+        return
+    cases = [
+        (syn._ranges([0x1000] * 5, [16] * 5, [2] * 5, [1] * 5), -11),
+        (syn._ranges([0x1000], [16], [syn.KIND_USER], [1]), -5),
+        (syn._ranges([0x1000, 0x1008], [16, 16], [2, 2], [1, 2]), -2),
+    ]
+    for r, c in cases:
+        with pytest.raises(ag.AgileError) as e:
+            ag.agile_guard_instrument_ptx(STREAM, "poison", apertures=(r.base, r.size, r.kind, r.ident))
+        assert e.value.code == c
+
+
 def test_skip_list_leaves_trusted_functions_alone():
     out, rep = ag.agile_guard_instrument_ptx(STREAM, "poison", skip=["agile_ptx_copy"])
     assert rep["guarded"] == 20 and rep["skipped"] == 8 and rep["functions"] == 3
