@@ -121,15 +121,17 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             // allowed. The others ("open") are decided in pass 2.
             uint32_t open = 0;
             if (g < ngroups) {
+                // Default-cached loads: pass 2 re-reads its accesses, which then hit L1 (with
+                // streaming loads they came from DRAM again, 40% more read traffic).
                 const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
                 uint64_t av[8];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {          // registers only: no indexed arrays
-                    const uint4 q = __ldcs(pa + k);
+                    const uint4 q = __ldg(pa + k);
                     av[2 * k] = (uint64_t)q.y << 32 | q.x;
                     av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
                 }
-                const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
+                const uint64_t wv = __ldg(reinterpret_cast<const unsigned long long *>(width + g * 8));
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
