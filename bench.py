@@ -319,7 +319,7 @@ def run_ours(args, ws, rank, local):
     serving = serve_sweep(ag, torch, dev) if "serving" in args.legs else None
 
     # end to end through host buffers: H2D of b, c, the three guarded kernels, D2H of a
-    e2e = end_to_end(torch, ws, dev, stream, step, A, B, C, max(3, min(args.steps // 100, 10))) \
+    e2e = end_to_end(ag, torch, ws, dev, stream, dtab, log, A, B, C, max(3, min(args.steps // 100, 10))) \
         if "e2e" in args.legs else None
 
     cpu = None
@@ -355,9 +355,11 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def end_to_end(torch, ws, dev, stream, step, A, B, C, steps):
-    """The workload through the public API from pinned host buffers: every step copies b
-    and c in, runs the three guarded kernels and copies a out."""
+def end_to_end(ag, torch, ws, dev, stream, dtab, log, A, B, C, steps):
+    """The workload through the public API from pinned host buffers, every step:
+    agile_stream_launch_host runs copy with b from the host, scale on the device-resident
+    b, and triad with c from the host and a back to the host. Each call cuts its arrays
+    into chunks whose copies in, guarded kernels and copies out overlap on three streams."""
     hb = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
     hc = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
     ha = torch.empty(N_ELEMS, dtype=torch.float32, pin_memory=True)
@@ -365,26 +367,30 @@ def end_to_end(torch, ws, dev, stream, step, A, B, C, steps):
     hc.copy_(C.cpu())
 
     def one():
-        B.copy_(hb, non_blocking=True)
-        C.copy_(hc, non_blocking=True)
-        step(True)
-        ha.copy_(A, non_blocking=True)
+        ag.agile_violation_log_init(log, 0, stream)
+        ag.agile_stream_launch_host("copy", dtab, A, B, C, None, hb, None, N_ELEMS, 3.0,
+                                    "poison", log, 0, stream)
+        ag.agile_stream_launch_host("scale", dtab, A, B, C, None, None, None, N_ELEMS, 3.0,
+                                    "poison", log, 0, stream)
+        ag.agile_stream_launch_host("triad", dtab, A, B, C, ha, None, hc, N_ELEMS, 3.0,
+                                    "poison", log, 0, stream)
 
-    with torch.cuda.stream(stream):
+    one()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
         one()
-        torch.cuda.synchronize()
-        barrier(ws)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            one()
-        e1.record(stream)
-        torch.cuda.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
     ms = max_over_ranks(ws, e0.elapsed_time(e1), dev)
+    rc, rec = ag.agile_violation_log_read(log, stream)
+    assert rc == 0 and rec.count == 0, "violation in the end-to-end run"
     return {"value": ws * STEP_BYTES * steps / (ms / 1e3) / 1e9, "unit": "GB/s",
             "h2d_bytes_per_step": 2 * 4 * N_ELEMS, "d2h_bytes_per_step": 4 * N_ELEMS,
-            "steps": steps}
+            "steps": steps, "api": "agile_stream_launch_host (chunks of 2^24 elements, 3 streams)"}
 
 
 def ptx_injected(ag, torch, dev, stream, dtab, log, A, B, C, reps=20):

@@ -257,6 +257,23 @@ AGILE_API int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *d
                         const float *d_c, size_t n, float s, int policy, void *d_log,
                         void *stream);
 
+/* agile_stream_launch over host arrays: the inputs come from host memory and the result
+ * goes back to it, with the copies inside the call. The n elements are cut into chunks of
+ * chunk_elems (a multiple of 4; 0 picks 2^24). Chunk k runs on one of three internal
+ * streams: copy h_b (and h_c for TRIAD) into d_b (d_c) at the chunk's offset, run the
+ * guarded kernel on the chunk, copy d_a back to h_a. So copies in both directions overlap
+ * with each other and with other chunks' kernels. A NULL h_b / h_c skips that input's copy
+ * (the device array already holds it); a NULL h_a skips the copy out. The kernel makes
+ * the same accesses at the same addresses as one launch over all n elements, so outputs
+ * and the log match it exactly. The device arrays are the ones the table guards. Pinned
+ * host memory is needed for the copies to overlap. Ordered after earlier work on `stream`;
+ * later work on `stream` waits for the whole call. Errors as agile_stream_launch, plus
+ * INVALID_ARG for chunk_elems not a multiple of 4. */
+AGILE_API int agile_stream_launch_host(int op, const agile_dev_table_t *tbl, float *d_a,
+                                       float *d_b, float *d_c, float *h_a, const float *h_b,
+                                       const float *h_c, size_t n, float s, int policy,
+                                       void *d_log, size_t chunk_elems, void *stream);
+
 enum { AGILE_IRR_GATHER = 0, AGILE_IRR_SCATTER = 1, AGILE_IRR_HIST = 2 };
 
 /* Irregular kernels with the guard fused in by hand (Sec. V-E), n elements, d_idx int64

@@ -125,6 +125,9 @@ _SIG = {
                                            ctypes.c_float, ctypes.c_int, _P, _P]),
     "agile_irregular_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
                                               ctypes.c_int, _P, _P]),
+    "agile_stream_launch_host": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
+                                                ctypes.c_size_t, ctypes.c_float, ctypes.c_int, _P,
+                                                ctypes.c_size_t, _P]),
     "agile_batch_device_bytes": (ctypes.c_size_t, [ctypes.c_size_t]),
     "agile_batch_upload": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, _P, ctypes.c_size_t, _P]),
     "agile_batch_launch": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
@@ -185,6 +188,15 @@ def _dptr(x) -> int | None:
         return None
     if isinstance(x, int):
         return x
+    return x.data_ptr()
+
+
+def _hptr(x) -> int | None:
+    """Host buffer address: None, an int, a numpy array or a CPU tensor."""
+    if x is None or isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
     return x.data_ptr()
 
 
@@ -373,6 +385,17 @@ def agile_stream_launch(op: str, dev: DevTable | None, d_a, d_b, d_c, n: int, s:
     _check(lib().agile_stream_launch(OPS[op], dev.ref if dev is not None else None, _dptr(d_a),
                                      _dptr(d_b), _dptr(d_c), n, s, POLICIES[policy], _dptr(d_log),
                                      _stream(stream)), "agile_stream_launch")
+
+
+def agile_stream_launch_host(op: str, dev: DevTable | None, d_a, d_b, d_c, h_a, h_b, h_c, n: int,
+                             s: float = 3.0, policy: str = "poison", d_log=None,
+                             chunk_elems: int = 0, stream=None) -> None:
+    """h_*: host buffers (pinned CPU tensors, numpy arrays or addresses) or None."""
+    _check(lib().agile_stream_launch_host(OPS[op], dev.ref if dev is not None else None,
+                                          _dptr(d_a), _dptr(d_b), _dptr(d_c), _hptr(h_a),
+                                          _hptr(h_b), _hptr(h_c), n, s, POLICIES[policy],
+                                          _dptr(d_log), chunk_elems, _stream(stream)),
+           "agile_stream_launch_host")
 
 
 def agile_irregular_launch(kind: str, dev: DevTable | None, d_idx, d_base, d_out, n: int,

@@ -136,3 +136,47 @@ def test_stream_rejects_misaligned_and_bad_args():
                                         1.0, 0, None, None) == -1
     assert ag.lib().agile_stream_launch(0, None, x.data_ptr(), x.data_ptr(), x.data_ptr(), 8,
                                         1.0, 9, None, None) == -1
+
+
+@pytest.mark.parametrize("chunk", [0, 4, 1 << 12])
+@pytest.mark.parametrize("policy", ["poison", "report"])
+def test_stream_from_host_equals_one_launch(chunk, policy):
+    """The host-array form: chunked copies in, guarded kernels, copies out, on three
+    streams. Outputs and the log equal one device launch over the whole arrays, with
+    violations in b, c and a, and a ragged tail."""
+    n = (1 << 18) + 3
+    _, _, nbytes = _hostile_layout(n, 0)
+    arena = _arena(nbytes)
+    base = arena.data_ptr()
+    r, va, _ = _hostile_layout(n, base)
+    _, dev = device_table(r, 12)
+    b, c = _fill(n, 91)
+    A, B, C = (_view(arena, va[k] - base, n) for k in "abc")
+    hb = torch.from_numpy(b).pin_memory()
+    hc = torch.from_numpy(c).pin_memory()
+    for op in OPS:
+        a0 = np.full(n, -5.0, np.float32)
+        # reference: one device launch
+        A.copy_(torch.from_numpy(a0)); B.copy_(hb); C.copy_(hc)
+        log = new_log(client=4)
+        ag.agile_stream_launch(op, dev, A, B, C, n, 3.0, policy, log)
+        rc, rec = ag.agile_violation_log_read(log)
+        want = A.cpu().numpy().copy()
+        # host form: device inputs cleared first, so they must come from the host
+        A.copy_(torch.from_numpy(a0)); B.zero_(); C.zero_()
+        ha = torch.empty(n, dtype=torch.float32).pin_memory()
+        log2 = new_log(client=4)
+        ag.agile_stream_launch_host(op, dev, A, B, C, ha, hb, hc, n, 3.0, policy, log2, chunk)
+        rc2, rec2 = ag.agile_violation_log_read(log2)
+        assert (ha.numpy().view(np.uint32) == want.view(np.uint32)).all(), op
+        assert (rc, rec.count, rec.key, rec.addr, rec.site, rec.verdict, rec.range_id) == \
+            (rc2, rec2.count, rec2.key, rec2.addr, rec2.site, rec2.verdict, rec2.range_id), op
+        exp, olog = oracle.stream(op, r, va, b, c if op == "triad" else None, a0, 3.0, policy)
+        assert (want.view(np.uint32) == exp.view(np.uint32)).all() and rec.count == olog.count
+
+
+def test_stream_from_host_rejects_bad_chunk():
+    x = torch.zeros(64, dtype=torch.float32, device=DEV)
+    with pytest.raises(ag.AgileError) as e:
+        ag.agile_stream_launch_host("copy", None, x, x, None, None, None, None, 64, chunk_elems=6)
+    assert e.value.code == -1
