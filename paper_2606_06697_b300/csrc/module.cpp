@@ -24,7 +24,7 @@ int agile_module_load(const char *ptx, agile_module_t **out) {
     *out = nullptr;
     agile_module *m = new (std::nothrow) agile_module;
     if (m == nullptr) return AGILE_ERR_NOMEM;
-    static char errlog[8192];
+    thread_local char errlog[8192];   // per thread: loads may run concurrently
     errlog[0] = '\0';
     cudaJitOption opt[2] = {cudaJitErrorLogBuffer, cudaJitErrorLogBufferSizeBytes};
     void *val[2] = {errlog, (void *)(uintptr_t)sizeof errlog};
