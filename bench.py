@@ -35,6 +35,7 @@ N_ELEMS = 1 << 28
 BYTES_PER_ELEM = {"copy": 8, "scale": 8, "triad": 12}
 STEP_BYTES = sum(BYTES_PER_ELEM.values()) * N_ELEMS
 PTX_STREAM = os.path.join(ROOT, "paper_2606_06697_b300", "ptx", "stream.ptx")
+PTX_IRREGULAR = os.path.join(ROOT, "paper_2606_06697_b300", "ptx", "irregular.ptx")
 METRIC = "guarded HBM GB/s (guarded streaming copy+scale+triad; guarded/unguarded ratio, " \
          "guard checks/s beside)"
 WORKLOAD = ("guarded streaming copy/scale/triad, 3 fp32 arrays of 2^28 elements (1 GiB each) "
@@ -505,6 +506,18 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
     log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
     useful = {"gather": 16, "scatter": 12, "hist": 8}
     res = {}
+    # the hand-written PTX kernels: instrumented with the table guard, with the aperture
+    # guard (the 4096 protected tails do not fit in four apertures, so the apertures are
+    # the first four of them: a cheaper check, not the same protection), and as written
+    import ctypes
+    src = open(PTX_IRREGULAR).read()
+    keep = np.flatnonzero(rr.kind != 0)[:4]
+    apset = (rr.base[keep], rr.size[keep], rr.kind[keep], rr.ident[keep])
+    ptx_mods = {"ptx_table_64KiB": ag.agile_module_load(ag.agile_guard_instrument_ptx(src, "poison")[0]),
+                "ptx_aperture4": ag.agile_module_load(ag.agile_guard_instrument_ptx(
+                    src, "poison", apertures=apset)[0]),
+                "ptx_plain": ag.agile_module_load(src)}
+    grid = torch.cuda.get_device_properties(dev).multi_processor_count * 4
     for dist in ("uniform", "zipf"):
         if dist == "uniform":
             rank = torch.randint(0, stripes * ue, (n,), generator=g, device=dev, dtype=torch.int64)
@@ -553,8 +566,34 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
                 row[label] = cell
             row["guarded_over_unguarded"] = row["unguarded"]["ms"] / min(
                 row["guarded_2MiB"]["ms"], row["guarded_64KiB"]["ms"])
+            args_ = [ctypes.c_uint64(idx.data_ptr()), ctypes.c_uint64(target),
+                     ctypes.c_uint64(out_t.data_ptr()), ctypes.c_uint64(n)]
+            for label, mod in ptx_mods.items():
+                if label != "ptx_plain":
+                    ag.agile_module_bind(mod, tabs[16][2] if label == "ptx_table_64KiB" else None, log)
+
+                def once_ptx():
+                    ag.agile_module_launch(mod, f"agile_ptx_{kind}", grid, 512, args_, stream)
+                if kind == "hist":
+                    bins_t.zero_()
+                once_ptx()
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    once_ptx()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                row[label] = {"ms": ms, "useful_gbs": useful[kind] * n / ms / 1e6}
+            row["ptx_table_over_plain"] = row["ptx_plain"]["ms"] / row["ptx_table_64KiB"]["ms"]
             res[f"{kind}_{dist}"] = row
         del element, key
+    for mod in ptx_mods.values():
+        mod.unload()
     del arena
     torch.cuda.empty_cache()
     return res

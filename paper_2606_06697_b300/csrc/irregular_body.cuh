@@ -40,6 +40,10 @@ __device__ __forceinline__ uint64_t remapped(const TView &V, const agile_dev_tab
     }
 }
 
+__device__ __forceinline__ void red_add1(void *p) {
+    asm volatile("red.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+
 template <int KIND, int POLICY>
 __device__ __forceinline__ float element(const TView &V, float *addr, bool ok, int64_t e,
                                          const agile_dev_table_t &T) {
@@ -59,9 +63,9 @@ __device__ __forceinline__ float element(const TView &V, float *addr, bool ok, i
         else if constexpr (POLICY == AGILE_POLICY_SINK) *reinterpret_cast<float *>(T.sink_page) = f;
         return 0.f;
     } else {
-        if (ok || kAlways) atomicAdd(reinterpret_cast<unsigned int *>(addr), 1u);
-        else if constexpr (POLICY == AGILE_POLICY_SINK)
-            atomicAdd(reinterpret_cast<unsigned int *>(T.sink_page), 1u);
+        // a reduction with no return value (red), so the lane does not wait for it
+        if (ok || kAlways) red_add1(addr);
+        else if constexpr (POLICY == AGILE_POLICY_SINK) red_add1(T.sink_page);
         return 0.f;
     }
 }
@@ -75,20 +79,29 @@ __device__ __forceinline__ const P *load_src(const TView &V, const agile_dev_tab
     return a2 ? reinterpret_cast<const P *>(a2) : reinterpret_cast<const P *>(T.zero_page);
 }
 
-// Units u0 .. u0+31 (one per lane, clipped to n4). Warp-collective only in its uniform
-// span checks; `spans` off means every index/output access is checked per lane.
+// A lane's group after its index loads: the four element offsets and whether the
+// output store is allowed.
+struct IrrGroup {
+    int64_t e[4];
+    size_t u;
+    bool act, oko;
+};
+
+// First half of a group (units u0 .. u0+31, one per lane, clipped to n4): the span checks
+// and the two 16-byte index loads. Warp-collective only in its uniform span checks;
+// `spans` off means every index/output access is checked per lane.
 template <int KIND, bool GUARD, int POLICY>
-__device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_table_t &T,
-                                                const int64_t *idx, float *base, float *out,
-                                                size_t u0, size_t n4, LaneLog &ll, bool spans) {
-    constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
+__device__ __forceinline__ IrrGroup irregular_load(const TView &V, const agile_dev_table_t &T,
+                                                   const int64_t *idx, float *out, size_t u0,
+                                                   size_t n4, LaneLog &ll, bool spans) {
     constexpr bool kGather = KIND == AGILE_IRR_GATHER;
     const longlong2 *idx2 = reinterpret_cast<const longlong2 *>(idx);
-    const longlong2 *zero2 = reinterpret_cast<const longlong2 *>(T.zero_page);
     float4 *out4 = reinterpret_cast<float4 *>(out);
-    const size_t u = u0 + (threadIdx.x & 31);
-    const bool act = u < n4;
-    bool ok0 = true, ok1 = true, oko = true;
+    IrrGroup G;
+    G.u = u0 + (threadIdx.x & 31);
+    G.act = G.u < n4;
+    G.oko = true;
+    bool ok0 = true, ok1 = true;
     if constexpr (GUARD) {
         // A warp's span that stays inside one all-user block is decided by one bitmap word
         // (shared memory when staged); other spans by the page map.
@@ -96,27 +109,40 @@ __device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_
         const uint64_t si = (uint64_t)(idx2 + 2 * u0);
         const bool fast_i = full && (block_user_fast(V, si, 1024, user_bits(V, si)) ||
                                      span_allowed(V, si, 1024));
-        if (!fast_i && act) {
-            ok0 = lane_check(V, (uint64_t)(idx2 + 2 * u), 16, 0, ll);
-            ok1 = lane_check(V, (uint64_t)(idx2 + 2 * u + 1), 16, 1, ll);
+        if (!fast_i && G.act) {
+            ok0 = lane_check(V, (uint64_t)(idx2 + 2 * G.u), 16, 0, ll);
+            ok1 = lane_check(V, (uint64_t)(idx2 + 2 * G.u + 1), 16, 1, ll);
         }
         if constexpr (kGather) {
             const uint64_t so = (uint64_t)(out4 + u0);
             const bool fast_o = full && (block_user_fast(V, so, 512, user_bits(V, so)) ||
                                          span_allowed(V, so, 512));
-            if (!fast_o && act) oko = lane_check(V, (uint64_t)(out4 + u), 16, 3, ll);
+            if (!fast_o && G.act) G.oko = lane_check(V, (uint64_t)(out4 + G.u), 16, 3, ll);
         }
     }
-    if (!act) return;
-    const longlong2 p0 = __ldg(load_src<POLICY>(V, T, idx2 + 2 * u, ok0, 16));
-    const longlong2 p1 = __ldg(load_src<POLICY>(V, T, idx2 + 2 * u + 1, ok1, 16));
-    (void)zero2;
-    const int64_t e[4] = {p0.x, p0.y, p1.x, p1.y};
+    longlong2 p0 = {0, 0}, p1 = {0, 0};
+    if (G.act) {
+        p0 = __ldg(load_src<POLICY>(V, T, idx2 + 2 * G.u, ok0, 16));
+        p1 = __ldg(load_src<POLICY>(V, T, idx2 + 2 * G.u + 1, ok1, 16));
+    }
+    G.e[0] = p0.x; G.e[1] = p0.y; G.e[2] = p1.x; G.e[3] = p1.y;
+    return G;
+}
+
+// Second half: the four element accesses and gather's output store. Per lane.
+template <int KIND, bool GUARD, int POLICY>
+__device__ __forceinline__ void irregular_apply(const TView &V, const agile_dev_table_t &T,
+                                                const IrrGroup &G, float *base, float *out,
+                                                LaneLog &ll) {
+    constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
+    constexpr bool kGather = KIND == AGILE_IRR_GATHER;
+    if (!G.act) return;
+    float4 *out4 = reinterpret_cast<float4 *>(out);
     float *addr[4];
     bool ok[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        addr[k] = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)e[k]);
+        addr[k] = reinterpret_cast<float *>((uint64_t)base + 4 * (uint64_t)G.e[k]);
         ok[k] = true;
     }
     if constexpr (GUARD) {
@@ -134,18 +160,27 @@ __device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_
     }
     float v[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = element<KIND, POLICY>(V, addr[k], ok[k], e[k], T);
+    for (int k = 0; k < 4; ++k) v[k] = element<KIND, POLICY>(V, addr[k], ok[k], G.e[k], T);
     if constexpr (kGather) {
         const float4 o = make_float4(v[0], v[1], v[2], v[3]);
-        if (oko || kAlways) {
-            __stcs(out4 + u, o);
+        if (G.oko || kAlways) {
+            __stcs(out4 + G.u, o);
         } else if constexpr (POLICY == AGILE_POLICY_SINK) {
             __stcs(reinterpret_cast<float4 *>(T.sink_page), o);
         } else if constexpr (POLICY == AGILE_POLICY_REMAP_OR) {
-            const uint64_t a2 = remapped<POLICY>(V, T, (uint64_t)(out4 + u), 16);
+            const uint64_t a2 = remapped<POLICY>(V, T, (uint64_t)(out4 + G.u), 16);
             if (a2) __stcs(reinterpret_cast<float4 *>(a2), o);
         }
     }
+}
+
+// One group: load, then apply. Warp-collective only in its uniform span checks.
+template <int KIND, bool GUARD, int POLICY>
+__device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_table_t &T,
+                                                const int64_t *idx, float *base, float *out,
+                                                size_t u0, size_t n4, LaneLog &ll, bool spans) {
+    const IrrGroup G = irregular_load<KIND, GUARD, POLICY>(V, T, idx, out, u0, n4, ll, spans);
+    irregular_apply<KIND, GUARD, POLICY>(V, T, G, base, out, ll);
 }
 
 // The n mod 4 tail elements, lanes 0..2 of one warp.

@@ -18,6 +18,7 @@
 // The table's device address is read once per function from the module global
 // __agile_guard_table; site = the access's position in its function.
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -29,6 +30,18 @@
 #include "ptx_guard_check.inc"
 
 namespace {
+
+// The injected PTX reads the table header by byte offset.
+static_assert(offsetof(agile_dev_table_t, lo) == 0 && offsetof(agile_dev_table_t, n) == 20 &&
+                  offsetof(agile_dev_table_t, base) == 32 && offsetof(agile_dev_table_t, end) == 40 &&
+                  offsetof(agile_dev_table_t, kind) == 48 && offsetof(agile_dev_table_t, id) == 56 &&
+                  offsetof(agile_dev_table_t, zero_page) == 64 &&
+                  offsetof(agile_dev_table_t, sink_page) == 72 &&
+                  offsetof(agile_dev_table_t, remap_or) == 104 &&
+                  offsetof(agile_dev_table_t, ubits) == 112 &&
+                  offsetof(agile_dev_table_t, ubits_log2) == 120 &&
+                  offsetof(agile_dev_table_t, ubits_n) == 124,
+              "header offsets used by the injected PTX");
 
 struct Fail {
     int code;
@@ -309,13 +322,17 @@ class Rewriter {
                    "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
                    "\tmov.u64 %__agT3, __agile_zero_page;\n"
                    "\tmov.u64 %__agT4, __agile_sink_page;\n";
+        // The fast test reads the all-user block bitmap: T0 = window start, T1 = blocks
+        // in the window, T2 = bitmap, lg = log2 of the block size, T5 = block size,
+        // T6 = block size - 1 (header offsets 0, 124, 112, 120).
         return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<8>;\n"
                "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
                "\tld.global.u64 %__agT7, [__agile_guard_table];\n"
                "\tld.global.u64 %__agT0, [%__agT7];\n"
-               "\tld.global.u64 %__agT1, [%__agT7+8];\n"
-               "\tld.global.u32 %__agTlg, [%__agT7+16];\n"
-               "\tld.global.u64 %__agT2, [%__agT7+24];\n"
+               "\tld.global.u32 %__agr0, [%__agT7+124];\n"
+               "\tcvt.u64.u32 %__agT1, %__agr0;\n"
+               "\tld.global.u32 %__agTlg, [%__agT7+120];\n"
+               "\tld.global.u64 %__agT2, [%__agT7+112];\n"
                "\tld.global.u64 %__agT3, [%__agT7+64];\n"
                "\tld.global.u64 %__agT4, [%__agT7+72];\n"
                "\tmov.b64 %__agT5, 1;\n"
@@ -561,18 +578,21 @@ class Rewriter {
                  "\tor.pred %__agp1, %__agp1, %__agp0;\n"
                  "\tsetp.ge.u64 %__agp0, %__agd1, %__agd0;\n"
                  "\tand.pred %__agp1, %__agp1, %__agp0;\n";
-        } else g += "\tsub.s64 %__agd1, %__agd0, %__agT0;\n"
-             "\tshr.u64 %__agd2, %__agd1, %__agTlg;\n"
-             "\tsetp.lt.u64 %__agp0, %__agd2, %__agT1;\n"
-             "\tmov.b32 %__agr0, 0;\n"
-             "\t@%__agp0 shl.b64 %__agd3, %__agd2, 2;\n"
-             "\t@%__agp0 add.s64 %__agd3, %__agd3, %__agT2;\n"
-             "\t@%__agp0 ld.global.nc.u32 %__agr0, [%__agd3];\n"
+        } else g += "\tsub.s64 %__agd1, %__agd0, %__agT0;\n"       // offset in the window
+             "\tshr.u64 %__agd2, %__agd1, %__agTlg;\n"                   // block
+             "\tmin.u64 %__agd2, %__agd2, %__agT1;\n"                    // past the window: last bit (clear)
+             "\tshr.u64 %__agd3, %__agd2, 5;\n"
+             "\tshl.b64 %__agd3, %__agd3, 2;\n"
+             "\tadd.s64 %__agd3, %__agd3, %__agT2;\n"
+             "\tld.global.nc.u32 %__agr0, [%__agd3];\n"
+             "\tcvt.u32.u64 %__agr1, %__agd2;\n"
+             "\tand.b32 %__agr1, %__agr1, 31;\n"
+             "\tshr.b32 %__agr0, %__agr0, %__agr1;\n"
+             "\tand.b32 %__agr0, %__agr0, 1;\n"
              "\tand.b64 %__agd4, %__agd1, %__agT6;\n"
              "\tadd.s64 %__agd4, %__agd4, " + W + ";\n"
              "\tsetp.le.u64 %__agp1, %__agd4, %__agT5;\n"
-             "\tshr.u32 %__agr1, %__agr0, 30;\n"
-             "\tsetp.eq.and.u32 %__agp1, %__agr1, 1, %__agp1;\n";
+             "\tsetp.ne.and.u32 %__agp1, %__agr0, 0, %__agp1;\n";
         if (acc.generic)
             g += "\tisspacep.global %__agp2, %__agd0;\n"
                  "\tnot.pred %__agp2, %__agp2;\n"
