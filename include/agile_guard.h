@@ -214,6 +214,16 @@ AGILE_API int agile_violation_log_init(void *d_log, uint32_t client, void *strea
  * and AGILE_ERR_TIMEOUT when a kernel's bounded wait gave up. */
 AGILE_API int agile_violation_log_read(const void *d_log, agile_violation_record_t *h_out, void *stream);
 
+/* Self-test of the kernels' bounded waits (failure detection without a GPU fault). One
+ * warp waits on an mbarrier that expects 16 bytes no copy will deliver -- the guard's
+ * staging wait, limited to 0.25 s -- and polls *d_flag (4-byte aligned device memory)
+ * for up to flag_us microseconds (1 .. 1e6). Each wait that gives up sets
+ * AGILE_LOG_STATUS_TIMEOUT in d_log's status, so agile_violation_log_read then returns
+ * AGILE_ERR_TIMEOUT; *d_result gets bit 0 for the barrier and bit 1 for the flag. The
+ * kernel always returns; no copy is left in flight. */
+AGILE_API int agile_selftest_bounded_waits(void *d_log, const uint32_t *d_flag, uint32_t flag_us,
+                                           uint32_t *d_result, void *stream);
+
 /* ---------------------------------------------------------------- device checks */
 
 /* Batched guard check: verdict[i] for the access [d_addr[i], d_addr[i] + d_width[i])

@@ -150,6 +150,7 @@ _SIG = {
     "agile_module_launch": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32,
                                            _P, _P]),
     "agile_module_unload": (None, [_P]),
+    "agile_selftest_bounded_waits": (ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P]),
     "agile_free": (None, [_P]),
     "agile_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "agile_version": (ctypes.c_uint32, []),
@@ -620,3 +621,9 @@ def agile_module_launch(m: Module, name: str, grid: int, block: int, args, strea
                                                    for a in args])
     _check(lib().agile_module_launch(m.handle, name.encode(), grid, block, arr, _stream(stream)),
            "agile_module_launch")
+
+
+def agile_selftest_bounded_waits(d_log, d_flag, flag_us: int, d_result, stream=None) -> None:
+    _check(lib().agile_selftest_bounded_waits(_dptr(d_log), _dptr(d_flag), flag_us,
+                                              _dptr(d_result), _stream(stream)),
+           "agile_selftest_bounded_waits")
