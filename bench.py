@@ -594,9 +594,71 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
         del element, key
     for mod in ptx_mods.values():
         mod.unload()
-    del arena
+    del arena, idx, out_t, bins_t
+    torch.cuda.empty_cache()
+    res["gather_uniform_stress_60k_4k"] = irregular_stress(ag, torch, dev, stream, n, reps)
     torch.cuda.empty_cache()
     return res
+
+
+def irregular_stress(ag, torch, dev, stream, n, reps, stripes=1 << 18):
+    """The adversarial variant of the irregular table: 2^18 stripes of a 60 KiB user range
+    and a 4 KiB protected range (16 GiB, 524288 ranges), uniform gather of 2^28 indices,
+    0.1% into the protected ranges. With 64 KiB pages (and bitmap blocks) no page is all
+    user; 4 KiB pages make every page pure again."""
+    user, prot = 60 << 10, 4 << 10
+    r, span, off = syn.irregular_layout(n, stripes, user, prot, 1 << 10)
+    arena = torch.empty(span, dtype=torch.uint8, device=dev)
+    base = arena.data_ptr()
+    g = torch.Generator(device=dev).manual_seed(syn.SEED_BASE + 13)
+    arena[:off["bins"]].view(torch.float32).uniform_(1, 2, generator=g)
+    ue, se, pe = user // 4, (user + prot) // 4, prot // 4
+    rank = torch.randint(0, stripes * ue, (n,), generator=g, device=dev, dtype=torch.int64)
+    idx = arena[off["idx"]:off["idx"] + 8 * n].view(torch.int64)
+    idx.copy_((rank // ue) * se + rank % ue)
+    del rank
+    bad = torch.unique(torch.randint(0, n, (n // 1000,), generator=g, device=dev))
+    idx[bad] = torch.randint(0, stripes, (bad.numel(),), generator=g, device=dev) * se + ue + \
+        torch.randint(0, pe, (bad.numel(),), generator=g, device=dev)
+    out_t = arena[off["out"]:off["out"] + 4 * n].view(torch.float32)
+    rr = r.shifted(base)
+    log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
+    row = {"ranges": int(len(rr.base))}
+    for label, lg in (("unguarded", None), ("guarded_4KiB", 12), ("guarded_64KiB", 16)):
+        dtab = None
+        if lg:
+            t = ag.agile_guard_table_build(rr.base, rr.size, rr.kind, rr.ident, lg)
+            tb = torch.empty(t.device_bytes(), dtype=torch.uint8, device=dev)
+            dtab = t.upload(tb, stream)
+
+        def once():
+            if lg:
+                ag.agile_violation_log_init(log, 0, stream)
+            ag.agile_irregular_launch("gather", dtab, idx, base, out_t, n, "poison",
+                                      log if lg else None, stream)
+        once()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            once()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        cell = {"ms": ms, "useful_gbs": 16 * n / ms / 1e6}
+        if lg:
+            rc, rec = ag.agile_violation_log_read(log, stream)
+            assert rec.count == bad.numel(), (label, rec.count, bad.numel())
+            cell["violations"] = rec.count
+        row[label] = cell
+    row["guarded_over_unguarded"] = row["unguarded"]["ms"] / min(
+        row["guarded_4KiB"]["ms"], row["guarded_64KiB"]["ms"])
+    del arena
+    torch.cuda.empty_cache()
+    return row
 
 
 def serve_sweep(ag, torch, dev, rates=(1e3, 3e3, 1e4, 3e4, 1e5), window_s=0.3):

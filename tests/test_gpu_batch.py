@@ -117,3 +117,26 @@ def test_batch_no_violation_log_empty():
     _, dev = device_table(t, 21)
     v, rc, rec = run_batch(dev, addr, width)
     assert (v == 0).all() and rc == 0 and rec.count == 0 and rec.range_id == ag.NO_RANGE
+
+
+@pytest.mark.parametrize("log2_page", [12, 16, 21])
+def test_batch_full_size_as_benchmarked(log2_page):
+    """2^28 checks, the benchmark's input (1M generated accesses repeated): every verdict
+    equals its access's generator label, and the log holds the first denial and the
+    exact count."""
+    t = syn.batch_table()
+    m, n = 1 << 20, 1 << 28
+    addr, width, label = syn.batch_accesses(t, m)
+    _, dev = device_table(t, log2_page)
+    da = torch.from_numpy(addr.view(np.int64)).to(DEV).repeat(n // m)
+    dw = torch.from_numpy(width).to(DEV).repeat(n // m)
+    dv = torch.empty(n, dtype=torch.uint8, device=DEV)
+    log = new_log()
+    ag.agile_guard_check_batch(dev, da, dw, n, dv, log)
+    rc, rec = ag.agile_violation_log_read(log)
+    lab = torch.from_numpy(label).to(DEV)
+    assert torch.equal(dv.view(n // m, m), lab.expand(n // m, m))
+    first = int(np.flatnonzero(label)[0])
+    assert rc == 1 and rec.count == (n // m) * int((label != 0).sum())
+    assert (rec.key, rec.addr, rec.width, rec.verdict) == \
+        (first, int(addr[first]), int(width[first]), int(label[first]))

@@ -184,3 +184,12 @@ def test_remap_policy_refused_where_unsupported():
     x = arena[off["out"]:off["out"] + 256].view(torch.float32)
     with pytest.raises(ag.AgileError):
         ag.agile_stream_launch("copy", dev, x, x, None, 64, 1.0, "remap")
+
+
+@pytest.mark.parametrize("kind", ["gather", "scatter", "hist"])
+@pytest.mark.parametrize("log2_page", [12, 16])
+def test_irregular_stress_layout(kind, log2_page):
+    """The adversarial 60 KiB user + 4 KiB protected stripes: with 64 KiB pages and
+    bitmap blocks no page is all user, so every element takes the full classification."""
+    run_case(kind, "poison", 40_003, log2_page, stripes=256, user=60 * 1024, prot=4 * 1024,
+             bins=1 << 10, frac_bad=0.01)
