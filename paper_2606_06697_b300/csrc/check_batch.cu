@@ -2,15 +2,15 @@
 // as the kernel guard of Sec. V-E applies it, with the first violation (smallest index)
 // and the violation count in the log.
 //
-// Launch shape: 512 threads, two blocks per SM, a grid-stride loop. Each lane handles
-// VEC consecutive accesses: VEC = 8 reads 64 address bytes as four 16-byte loads, 8 width
-// bytes as one 8-byte load and writes 8 verdict bytes as one 8-byte store. The whole
-// table (page map and range arrays) is staged into shared memory by bulk copies when it
-// fits in 96 KiB, so the classification -- page lookup, and a short binary search on
-// mixed pages -- runs inline on shared memory; tables whose window spans under 4 GiB
-// stage 32-bit copies of the range bounds instead and decide allowed accesses in 32-bit
-// arithmetic. Each thread keeps its smallest violation in registers; the block reduces
-// them once at the end.
+// Launch shape: one 1024-thread block per SM, a warp-uniform grid-stride loop. Each lane
+// takes 8 consecutive accesses per round: four 16-byte address loads, one 8-byte width
+// load, one 8-byte verdict store. Staged into shared memory by bulk copies: the page map,
+// the packed range records (windows under 4 GiB; otherwise the range arrays) and the
+// all-user block bitmap. Pass 1 decides the accesses inside all-user blocks from the
+// bitmap, without branches; pass 2 deals the warp's remaining accesses out over its lanes
+// and decides each by the full rule (the 32-bit uniform decision over the packed records
+// where it applies). Each thread keeps its smallest violation in registers; the block
+// reduces them once at the end.
 #include <cuda_runtime.h>
 
 #include "agile_internal.h"
@@ -22,7 +22,8 @@ using agile::LaneLog;
 using agile::LogDev;
 using agile::TView;
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;   // one block per SM: measured 250 G checks/s at 2^28,
+                                 // against 231 for 2 x 512 and 218 for 4 x 256
 
 // Uniform decision in 32-bit arithmetic, for tables whose window spans under 4 GiB (the
 // packed records hold each range's start and last byte as offsets from the window start,
@@ -99,7 +100,7 @@ __device__ __forceinline__ uint32_t full_one(const TView &V, uint64_t a, uint32_
 }
 
 template <int MODE, int VEC>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
               const uint8_t *__restrict__ width, uint8_t *__restrict__ verdict, size_t n,
               LogDev *log) {
@@ -201,7 +202,7 @@ int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size
     }
     size_t groups = n / VEC;
     size_t want = (groups + kThreads - 1) / kThreads;
-    size_t cap = (size_t)agile::sm_count() * 2;
+    size_t cap = (size_t)agile::sm_count();
     unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
     k_check_batch<MODE, VEC><<<blocks, kThreads, smem, st>>>(T, a, w, v, n, log);
     AGILE_CUDA_TRY(cudaGetLastError());
