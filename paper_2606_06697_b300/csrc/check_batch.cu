@@ -22,8 +22,8 @@ using agile::LaneLog;
 using agile::LogDev;
 using agile::TView;
 
-constexpr int kThreads = 1024;   // one block per SM: measured 250 G checks/s at 2^28,
-                                 // against 231 for 2 x 512 and 218 for 4 x 256
+constexpr int kThreads = 1024;   // one block per SM: 250 G checks/s at 2^28 against 231
+                                 // for 2 x 512 and 218 for 4 x 256 (same code otherwise)
 
 // Uniform decision in 32-bit arithmetic, for tables whose window spans under 4 GiB (the
 // packed records hold each range's start and last byte as offsets from the window start,
@@ -83,6 +83,16 @@ __device__ __forceinline__ bool decide32(const TView &V, uint64_t a, uint32_t w,
     return true;
 }
 
+// The bitmap test of pass 1 for windows under 4 GiB (the packed-record tables): one 64-bit
+// window check, then 32-bit arithmetic (blocks there are at most 2^14 bytes).
+__device__ __forceinline__ bool user_fast32(const TView &V, uint64_t a, uint32_t w) {
+    const uint64_t off = a - V.lo;
+    const uint32_t o = (uint32_t)off;
+    const uint32_t k = off <= V.last - V.lo ? o >> V.ulg : V.un;   // outside: the clear bit
+    const uint32_t m = (1u << V.ulg) - 1u;
+    return ((V.ubits[k >> 5] >> (k & 31)) & 1u) && (o & m) + w <= m + 1u;
+}
+
 __device__ __forceinline__ bool legal_width(uint32_t w) {
     return w <= 16 && ((0x10116u >> w) & 1u);        // 1, 2, 4, 8, 16
 }
@@ -136,8 +146,10 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
-                    const bool ok = legal_width(w) && av[k] <= ~0ull - w &&
-                                    agile::block_user_fast(V, av[k], w, agile::user_bits(V, av[k]));
+                    bool inb;
+                    if constexpr (kC32) inb = user_fast32(V, av[k], w);
+                    else inb = agile::block_user_fast(V, av[k], w, agile::user_bits(V, av[k]));
+                    const bool ok = legal_width(w) && av[k] <= ~0ull - w && inb;
                     open |= (uint32_t)!ok << k;
                 }
                 __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), 0ull);
