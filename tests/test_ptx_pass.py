@@ -234,3 +234,66 @@ $L2: ld.global.f32 %f1, [%rd1+4];
     assert rep["guarded"] == 2
     assert "$L1:" in out and "$L2:" in out
     assemble(out)
+
+
+def _random_body(rng, n_stmt):
+    """Random statements over global, generic, shared, local and const accesses, some
+    predicated, with vector forms and offsets. Returns (body, n_global, n_generic)."""
+    loads = [("u8", "%rs1"), ("u16", "%rs2"), ("u32", "%r1"), ("u64", "%rd5"), ("f32", "%f1"),
+             ("v2.f32", "{%f2, %f3}"), ("v4.f32", "{%f4, %f5, %f6, %f7}"), ("v2.u64", "{%rd6, %rd7}")]
+    stores = [("u8", "%rs1"), ("u32", "%r1"), ("f32", "%f1"), ("v2.f32", "{%f2, %f3}"),
+              ("v4.f32", "{%f4, %f5, %f6, %f7}"), ("u64", "%rd5")]
+    lines, ng, ngen = [], 0, 0
+    for _ in range(n_stmt):
+        pred = rng.choice(["", "", "@%p1 ", "@!%p1 "])
+        off = rng.choice(["", "+8", "+-16", "+4096"])
+        base = rng.choice(["%rd1", "%rd2"])
+        kind = rng.randrange(9)
+        if kind == 0:
+            t, d = rng.choice(loads)
+            nc = rng.choice(["", ".nc"])
+            lines.append(f"{pred}ld.global{nc}.{t} {d}, [{base}{off}];"); ng += 1
+        elif kind == 1:
+            t, sv = rng.choice(stores)
+            lines.append(f"{pred}st.global.{t} [{base}{off}], {sv};"); ng += 1
+        elif kind == 2:
+            lines.append(f"{pred}atom.global.add.u32 %r2, [{base}{off}], 1;"); ng += 1
+        elif kind == 3:
+            lines.append(f"{pred}red.global.add.u32 [{base}{off}], %r1;"); ng += 1
+        elif kind == 4:
+            lines.append(f"{pred}ld.f32 %f1, [{base}{off}];"); ng += 1; ngen += 1
+        elif kind == 5:
+            lines.append(f"{pred}st.u32 [{base}{off}], %r1;"); ng += 1; ngen += 1
+        elif kind == 6:
+            lines.append(f"{pred}ld.shared.f32 %f1, [%r3];")
+        elif kind == 7:
+            lines.append(f"{pred}ld.local.u32 %r1, [%rd3];")
+        else:
+            lines.append("add.f32 %f1, %f1, %f2;")
+    return "\n".join(lines), ng, ngen
+
+
+RAND_REGS = (".reg .b64 %rd<8>;\n.reg .f32 %f<8>;\n.reg .b32 %r<4>;\n.reg .b16 %rs<3>;\n"
+             ".reg .pred %p<2>;\nsetp.ne.u64 %p1, %rd1, 0;\nmov.u64 %rd2, %rd1;\nmov.u32 %r3, 0;\n"
+             "mov.u64 %rd3, 0;")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_kernels_every_global_access_guarded(seed):
+    """Random mixes of access forms: the report counts exactly the global and generic
+    accesses, each gets one site, other spaces stay untouched, and the output assembles
+    for sm_103a under every policy and under the aperture rule."""
+    import random
+    import agile_synth as syn
+    rng = random.Random(1000 + seed)
+    body, ng, ngen = _random_body(rng, 40)
+    src = kernel(body, RAND_REGS)
+    ap = syn.table1_protected()
+    variants = [(p, None) for p in ("poison", "sink", "report", "trap", "remap")]
+    variants += [(p, (ap.base, ap.size, ap.kind, ap.ident)) for p in ("poison", "report")]
+    for policy, aps in variants:
+        out, rep = ag.agile_guard_instrument_ptx(src, policy, apertures=aps)
+        assert rep["guarded"] == ng and rep["generic_guarded"] == ngen, (policy, rep)
+        assert len(sites(out)) == ng
+        assert out.count("ld.shared.f32 %f1, [%r3];") == body.count("ld.shared.f32 %f1, [%r3];")
+        assemble(out)
