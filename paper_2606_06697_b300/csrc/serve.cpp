@@ -182,10 +182,12 @@ struct agile_worker {
         }
         const uint64_t hdr[8] = {n, pre[n], 0, cfg.tile, 0, 0, 0, 0};
         std::memcpy(s.staging, hdr, 64);
-        cudaMemcpyAsync(s.dev, s.staging, 64 + 64 * n + 8 * (n + 1), cudaMemcpyHostToDevice, s.stream);
         agile_batch_config_t bc{cfg.tile, 1, 2, 0};
-        const int rc = agile_batch_launch(s.dev, n, &bc, s.stream);
-        cudaEventRecord(s.done, s.stream);
+        int rc = cudaMemcpyAsync(s.dev, s.staging, 64 + 64 * n + 8 * (n + 1), cudaMemcpyHostToDevice,
+                                 s.stream) == cudaSuccess
+                     ? agile_batch_launch(s.dev, n, &bc, s.stream)
+                     : AGILE_ERR_CUDA;
+        if (cudaEventRecord(s.done, s.stream) != cudaSuccess && rc == AGILE_OK) rc = AGILE_ERR_CUDA;
         const uint32_t seq = launches++;
         for (uint32_t id : batch) {
             comp[id].admit_ns = t;
