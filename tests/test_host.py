@@ -181,3 +181,20 @@ def test_aperture_set_rejected_before_launch(bad, code):
         ag.agile_aperture_check_batch((bad.base, bad.size, bad.kind, bad.ident), 0x1000, 0x2000, 8,
                                       0x3000)
     assert e.value.code == code
+
+
+def test_host_array_and_selftest_arguments_checked_before_launch():
+    """Argument errors of the host-array entry point and the bounded-wait self-test come
+    back from the host side, before anything is queued on a device."""
+    lib = ag.lib()
+    assert lib.agile_stream_launch_host(7, None, 0x1000, 0x1000, None, None, None, None, 64,
+                                        1.0, 0, None, 0, None) == -1          # unknown op
+    assert lib.agile_stream_launch_host(0, None, 0x1000, 0x1000, None, None, None, None, 64,
+                                        1.0, 0, None, 6, None) == -1          # chunk % 4 != 0
+    assert lib.agile_stream_launch_host(0, None, 0x1000, 0x1000, None, None, None, None, 0,
+                                        1.0, 0, None, 0, None) == 0           # nothing to do
+    assert lib.agile_stream_launch_host(2, None, 0x1000, 0x1000, None, None, None, None, 64,
+                                        1.0, 0, None, 0, None) == -1          # triad without c
+    assert lib.agile_selftest_bounded_waits(0x1000, 0x2000, 0, 0x3000, None) == -1
+    assert lib.agile_selftest_bounded_waits(0x1000, 0x2000, 2_000_000, 0x3000, None) == -1
+    assert lib.agile_selftest_bounded_waits(0x1008, 0x2000, 100, 0x3000, None) == -12
