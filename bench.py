@@ -155,54 +155,119 @@ def max_over_ranks(ws, x, device):
 # ---------------------------------------------------------------- oracle timing
 
 
-def oracle_sample(n_sample: int, seed: int = 1):
-    """Oracle guarded copy/scale/triad over the first n_sample elements of the workload's
-    arrays, in the workload's arena layout. Returns (seconds, bytes)."""
+def host_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _chunks(n: int, parts: int, align: int = 4):
+    """Contiguous [lo, hi) pieces of range(n), boundaries multiples of `align`."""
+    cuts = [min(n, (n * k // parts) // align * align) for k in range(parts)] + [n]
+    return [(lo, hi) for lo, hi in zip(cuts, cuts[1:]) if hi > lo]
+
+
+def _parallel(fn, pieces, workers):
+    """fn over the pieces on `workers` threads. The oracle's C entry points release the
+    interpreter lock while they run, so the pieces run on separate cores."""
+    if workers <= 1:
+        return [fn(p) for p in pieces]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(fn, pieces))
+
+
+class StreamSample:
+    """The first n elements of the workload's b and c arrays, in the workload's arena
+    layout (a 1096-range table), for the oracle's guarded copy / scale / triad."""
+
+    def __init__(self, n: int, seed: int = 1):
+        r, span, off = syn.stream_layout(N_ELEMS)
+        self.base = 0x7F0000000000
+        self.table = r.shifted(self.base)
+        self.off = off
+        st = syn.Stream(seed, 8)
+        self.b = st.uniform(n).astype(np.float32)
+        self.c = st.uniform(n).astype(np.float32)
+        self.a0 = np.zeros(n, np.float32)
+        self.n = n
+
+    def run(self, workers: int):
+        """One step (copy, scale, triad) of the oracle over the sample, the elements cut
+        into one contiguous piece per thread. Returns (seconds, algorithmic bytes)."""
+        import oracle
+
+        def piece(op):
+            def f(p):
+                lo, hi = p
+                va = {k: self.base + self.off[k] + 4 * lo for k in "abc"}
+                return oracle.stream(op, self.table, va, self.b[lo:hi], self.c[lo:hi],
+                                     self.a0[lo:hi], 3.0, "poison")
+            return f
+        pieces = _chunks(self.n, workers)
+        t0 = time.perf_counter()
+        for op in ("copy", "scale", "triad"):
+            _parallel(piece(op), pieces, workers)
+        return time.perf_counter() - t0, sum(BYTES_PER_ELEM.values()) * self.n
+
+
+def cpu_batch_check(workers: int):
+    """The oracle's batch check on the 84-range table workload (10 B per check): the
+    sorted-interval form on every host thread over 2^24 accesses (the 1M generated
+    accesses repeated), and single-threaded on the 1M accesses themselves, both the
+    sorted form and the linear scan that defines the rule."""
     import oracle
-    r, span, off = syn.stream_layout(N_ELEMS)
-    base = 0x7F0000000000
-    t = r.shifted(base)
-    va = {k: base + v for k, v in off.items()}
-    st = syn.Stream(seed, 8)
-    b = st.uniform(n_sample).astype(np.float32)
-    c = st.uniform(n_sample).astype(np.float32)
-    a0 = np.zeros(n_sample, np.float32)
-    t0 = time.perf_counter()
-    for op in ("copy", "scale", "triad"):
-        oracle.stream(op, t, va, b, c, a0, 3.0, "poison")
-    dt = time.perf_counter() - t0
-    return dt, sum(BYTES_PER_ELEM.values()) * n_sample
+    t = syn.batch_table()
+    addr, width, _ = syn.batch_accesses(t, 1 << 20)
+    out = {}
+    for name, method, reps, w in (("linear_1_thread", "linear", 1, 1),
+                                  ("sorted_1_thread", "sorted", 1, 1),
+                                  ("sorted_all_threads", "sorted", 16, workers)):
+        A, W = np.tile(addr, reps), np.tile(width, reps)
+        pieces = _chunks(len(A), w, 1)
+        t0 = time.perf_counter()
+        _parallel(lambda p: oracle.check_batch(t, A[p[0]:p[1]], W[p[0]:p[1]], method=method),
+                  pieces, w)
+        dt = time.perf_counter() - t0
+        out[name] = {"checks_per_s": len(A) / dt, "accesses": len(A), "threads": w,
+                     "seconds": dt}
+    return out
 
 
 def run_reference(args, ws, rank):
-    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    """The oracle as the reference arm, on every host thread: each step a bounded sample
+    of the workload."""
     if rank != 0:
         return
     import oracle
     oracle.build()
-    dt, _ = oracle_sample(1 << 16)                       # calibrate
-    per_elem = dt / (1 << 16)
+    workers = host_threads()
+    dt, nb = StreamSample(1 << 20).run(workers)           # calibrate
+    per_elem = dt / (1 << 20)
     budget = 90.0 / max(args.steps + args.warmup, 1)     # whole run ~1.5 min
-    n_sample = int(max(1 << 12, min(1 << 24, budget / per_elem)))
+    n_sample = int(max(1 << 16, min(1 << 26, budget / per_elem)))
     n_sample -= n_sample % 4
+    sample = StreamSample(n_sample)
     for _ in range(args.warmup):
-        oracle_sample(n_sample)
+        sample.run(workers)
     tot_t, tot_b = 0.0, 0
     for _ in range(args.steps):
-        dt, nb = oracle_sample(n_sample)
+        dt, nb = sample.run(workers)
         tot_t += dt
         tot_b += nb
     value = tot_b / tot_t / 1e9
-    sample = (f"first {n_sample} elements of each array per step (of 2^28), same arena table; "
-              f"single-threaded oracle (sorted-interval search per 16-byte access)")
+    desc = (f"first {n_sample} elements of each array per step (of 2^28), same arena table; "
+            f"the oracle (sorted-interval search per 16-byte access) on {workers} host threads, "
+            f"one contiguous piece each")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": N_ELEMS, "sample_elements": n_sample},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": workers, "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -219,6 +284,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)        # torch's own work (fills, copies) goes on the same stream
     hbm_peak, peak_kind = peaks()
 
     r, span, off = syn.stream_layout(N_ELEMS)
@@ -237,20 +303,24 @@ def run_ours(args, ws, rank, local):
 
     ops = ("copy", "scale", "triad")
 
-    def step(guarded, ev=None):
+    def step(guarded, ev=None, shape=None):
         if guarded:
             ag.agile_violation_log_init(log, rank, stream)
         for op in ops:
             if ev is not None:
                 ev[op][0].record(stream)
-            ag.agile_stream_launch(op, dtab if guarded else None, A, B, C, N_ELEMS, 3.0,
-                                   "poison", log if guarded else None, stream)
+            if shape is None:
+                ag.agile_stream_launch(op, dtab if guarded else None, A, B, C, N_ELEMS, 3.0,
+                                       "poison", log if guarded else None, stream)
+            else:
+                ag.agile_stream_launch_shape(op, dtab if guarded else None, A, B, C, N_ELEMS, 3.0,
+                                             "poison", log if guarded else None, *shape, stream)
             if ev is not None:
                 ev[op][1].record(stream)
 
-    def timed(guarded, steps, warmup, per_kernel=False):
+    def timed(guarded, steps, warmup, per_kernel=False, shape=None):
         for _ in range(warmup):
-            step(guarded)
+            step(guarded, shape=shape)
         evs = []
         barrier(ws)
         torch.cuda.synchronize()
@@ -263,7 +333,7 @@ def run_ours(args, ws, rank, local):
                 ev = {op: (torch.cuda.Event(enable_timing=True),
                            torch.cuda.Event(enable_timing=True)) for op in ops}
                 evs.append(ev)
-            step(guarded, ev)
+            step(guarded, ev, shape)
         t1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
@@ -289,12 +359,23 @@ def run_ours(args, ws, rank, local):
                               "clocks": ck}), flush=True)
         return
 
-    # unguarded twins
+    # unguarded twins at both launch shapes (4 units x 2 blocks/SM is their own best shape,
+    # 8 x 1 is the guarded kernels'), and the guarded kernels at the unguarded shape
+    shapes = {"u8_b1": (8, 1), "u4_b2": (4, 2)}
+    by_shape = {}
+    kern_u, value_u = {op: None for op in ops}, None
     if "unguarded" in args.legs:
-        ms_u, kern_u = timed(False, max(args.steps // 2, 10), 3, per_kernel=True)
-        value_u = STEP_BYTES * max(args.steps // 2, 10) / (ms_u / 1e3) / 1e9
-    else:
-        kern_u, value_u = {op: None for op in ops}, None
+        k_u = max(args.steps // 2, 10)
+        for name, sh in shapes.items():
+            ms_s, kern_s = timed(False, k_u, 3, per_kernel=True, shape=sh)
+            by_shape[f"unguarded_{name}"] = {"gbs": STEP_BYTES * k_u / (ms_s / 1e3) / 1e9,
+                                             "kernel_ms": kern_s}
+        ms_s, kern_s = timed(True, k_u, 3, per_kernel=True, shape=shapes["u4_b2"])
+        by_shape["guarded_u4_b2"] = {"gbs": STEP_BYTES * k_u / (ms_s / 1e3) / 1e9, "kernel_ms": kern_s}
+        by_shape["guarded_u8_b1"] = {"gbs": value / ws, "kernel_ms": kern}
+        best = max(("u8_b1", "u4_b2"), key=lambda k: by_shape[f"unguarded_{k}"]["gbs"])
+        value_u = by_shape[f"unguarded_{best}"]["gbs"]
+        kern_u = by_shape[f"unguarded_{best}"]["kernel_ms"]
 
     # the same kernels from hand-written PTX through the guard pass (poison)
     ptx_kern, ptx_gbs, ptx_plain_gbs, ptx_ap_gbs = None, None, None, None
@@ -315,7 +396,10 @@ def run_ours(args, ws, rank, local):
     # batch check throughput: the 1M-access table workload and a 2^28-access stream
     batch = batch_throughput(ag, torch, dev, stream) if "batch" in args.legs else None
     irregular = irregular_sweep(ag, torch, dev, stream, n=args.irregular_n,
-                                stripes=args.irregular_stripes) if "irregular" in args.legs else None
+                                stripes=args.irregular_stripes, kinds=args.irregular_kinds.split(","),
+                                dists=args.irregular_dists.split(","),
+                                stress="gather" in args.irregular_kinds) \
+        if "irregular" in args.legs else None
     clients = batch_clients(ag, torch, dev, stream) if "clients" in args.legs else None
     serving = serve_sweep(ag, torch, dev) if "serving" in args.legs else None
 
@@ -327,13 +411,20 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and "cpu" in args.legs:
         import oracle
         oracle.build()
-        n_sample = 1 << 27
-        dt, nb = oracle_sample(n_sample)
-        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+        workers = host_threads()
+        n_all, n_one = 1 << 27, 1 << 25
+        dt, nb = StreamSample(n_all).run(workers)
+        dt1, nb1 = StreamSample(n_one).run(1)
+        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": workers, "kind": "oracle",
                "sample": f"guarded copy+scale+triad over the first 2^27 of the 2^28 elements, "
-                         f"same arena table, single-threaded oracle; {dt:.1f} s"}
+                         f"same arena table; the oracle on {workers} host threads (one "
+                         f"contiguous piece each), {dt:.1f} s",
+               "single_thread": {"value": nb1 / dt1 / 1e9, "unit": "GB/s", "cores": 1,
+                                 "sample": f"first 2^25 elements, {dt1:.1f} s"},
+               "batch_check": cpu_batch_check(workers)}
 
     if rank == 0:
+        hb = hbm_peak
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -341,19 +432,55 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": WORKLOAD, "elements": N_ELEMS, "table_ranges": len(r),
                        "page_bytes": 1 << 21, "policy": "poison",
                        "l2": "each array 1 GiB, larger than the 126 MB L2; no flush needed"},
-            "unguarded_gbs": value_u,
-            "guarded_over_unguarded": value / ws / value_u if value_u else None,
-            "ptx_injected_gbs": ptx_gbs, "ptx_plain_gbs": ptx_plain_gbs,
-            "ptx_injected_over_plain": ptx_gbs / ptx_plain_gbs if ptx_gbs else None,
-            "ptx_aperture_rule_gbs": ptx_ap_gbs,
-            "ptx_kernel_ms": ptx_kern,
+            # the full measurements first; the figures the targets are read from last
+            "serving": serving, "irregular": irregular, "batch_clients": clients,
+            "batch_check": batch, "ptx_kernel_ms": ptx_kern, "stream_shapes": by_shape,
             "kernel_ms": {f"{op}_guarded": kern[op] for op in ops} |
                          {f"{op}_unguarded": kern_u[op] for op in ops},
-            "roofline": roofline, "batch_check": batch, "irregular": irregular, "batch_clients": clients, "serving": serving,
-            "e2e": e2e,
-            "gpu_launches": args.steps * 4, "clocks": ck, "cpu_baseline": cpu,
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": args.steps * 4, "clocks": ck,
+            "targets": targets_summary(value / ws, value_u, by_shape, ptx_gbs, ptx_plain_gbs,
+                                       ptx_ap_gbs, batch, irregular, clients, serving, cpu, hb),
         }
         print(json.dumps(line), flush=True)
+
+
+def _r(x, d=3):
+    return None if x is None else round(float(x), d)
+
+
+def targets_summary(guarded, unguarded_best, by_shape, ptx_gbs, ptx_plain_gbs, ptx_ap_gbs,
+                    batch, irregular, clients, serving, cpu, hbm_peak):
+    """The ratios and rates the targets are judged on, compactly."""
+    t = {"guarded_gbs": _r(guarded, 1), "guarded_frac_of_peak": _r(guarded / hbm_peak),
+         "unguarded_best_gbs": _r(unguarded_best, 1),
+         "guarded_over_unguarded_best": _r(guarded / unguarded_best) if unguarded_best else None,
+         "unguarded_gbs_by_shape": {k[len("unguarded_"):]: _r(v["gbs"], 1)
+                                    for k, v in by_shape.items() if k.startswith("unguarded_")},
+         "ptx_table_over_plain": _r(ptx_gbs / ptx_plain_gbs) if ptx_gbs else None,
+         "ptx_aperture_over_plain": _r(ptx_ap_gbs / ptx_plain_gbs) if ptx_ap_gbs else None}
+    if batch:
+        t["batch_gchecks"] = {
+            size: {"table": _r(row[row["best"]]["checks_per_s"] / 1e9, 1),
+                   "table_frac_of_peak": _r(row[row["best"]]["gbs"] / hbm_peak),
+                   "aperture": _r(row["aperture_rule"]["checks_per_s"] / 1e9, 1)}
+            for size, row in batch.items()}
+    if irregular:
+        t["irregular_guarded_over_unguarded"] = {
+            k: _r(v["guarded_over_unguarded"]) for k, v in irregular.items()}
+        t["irregular_ptx_table_over_plain"] = {
+            k: _r(v["ptx_table_over_plain"]) for k, v in irregular.items() if "ptx_table_over_plain" in v}
+    if clients:
+        t["clients_graph_speedup"] = _r(clients["speedup_graph_vs_separate"], 2)
+    if serving:
+        t["serving_p99_us"] = {k: [_r(v["continuous"]["p99_us"], 0), _r(v["one_at_a_time"]["p99_us"], 0)]
+                               for k, v in serving.items() if isinstance(v, dict) and "continuous" in v}
+    if cpu:
+        t["cpu_oracle"] = {"all_threads_gbs": _r(cpu["value"]), "threads": cpu["cores"],
+                           "one_thread_gbs": _r(cpu["single_thread"]["value"]),
+                           "batch_mchecks_all_threads": _r(cpu["batch_check"]["sorted_all_threads"]["checks_per_s"] / 1e6, 1),
+                           "batch_mchecks_linear_1_thread": _r(cpu["batch_check"]["linear_1_thread"]["checks_per_s"] / 1e6, 1)}
+    return t
 
 
 def end_to_end(ag, torch, ws, dev, stream, dtab, log, A, B, C, steps):
@@ -482,7 +609,8 @@ def batch_clients(ag, torch, dev, stream, n_clients=256, reps=5):
 
 
 
-def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
+def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096,
+                    kinds=("gather", "scatter", "hist"), dists=("uniform", "zipf"), stress=True):
     """Gather / scatter / histogram over the 16 GiB striped table (4096 user allocations of
     4 MiB, each followed by a 64 KiB protected range), 2^28 int64 indices, uniform and
     Zipf(1.1), 0.1% aimed into protected ranges; guarded (poison, 2 MiB and 64 KiB pages)
@@ -518,7 +646,7 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
                     src, "poison", apertures=apset)[0]),
                 "ptx_plain": ag.agile_module_load(src)}
     grid = torch.cuda.get_device_properties(dev).multi_processor_count * 4
-    for dist in ("uniform", "zipf"):
+    for dist in dists:
         if dist == "uniform":
             rank = torch.randint(0, stripes * ue, (n,), generator=g, device=dev, dtype=torch.int64)
         else:
@@ -532,7 +660,7 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
             torch.randint(0, pe, (nb,), generator=g, device=dev)
         key[bad] = bins + torch.randint(0, pe, (nb,), generator=g, device=dev)
         del rank
-        for kind in ("gather", "scatter", "hist"):
+        for kind in kinds:
             idx.copy_(key if kind == "hist" else element)
             target = base + (off["bins"] if kind == "hist" else 0)
             row = {}
@@ -566,6 +694,29 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
                 row[label] = cell
             row["guarded_over_unguarded"] = row["unguarded"]["ms"] / min(
                 row["guarded_2MiB"]["ms"], row["guarded_64KiB"]["ms"])
+            # the same guarded kernel with the __match_any_sync bitmap read (64 KiB pages)
+            def once_match():
+                ag.agile_violation_log_init(log, 0, stream)
+                ag.agile_irregular_launch_fastpath(kind, tabs[16][2], idx, target, out_t, n, "poison",
+                                                   log, "match", stream)
+            if kind == "hist":
+                bins_t.zero_()
+            once_match()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                once_match()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            rc, rec = ag.agile_violation_log_read(log, stream)
+            assert rec.count == nb, ("match", kind, dist, rec.count, nb)
+            ms = statistics.median(ts)
+            row["guarded_64KiB_match"] = {"ms": ms, "useful_gbs": useful[kind] * n / ms / 1e6}
+            row["match_over_bitmap"] = row["guarded_64KiB"]["ms"] / ms
             args_ = [ctypes.c_uint64(idx.data_ptr()), ctypes.c_uint64(target),
                      ctypes.c_uint64(out_t.data_ptr()), ctypes.c_uint64(n)]
             for label, mod in ptx_mods.items():
@@ -596,8 +747,9 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096):
         mod.unload()
     del arena, idx, out_t, bins_t
     torch.cuda.empty_cache()
-    res["gather_uniform_stress_60k_4k"] = irregular_stress(ag, torch, dev, stream, n, reps)
-    torch.cuda.empty_cache()
+    if stress:
+        res["gather_uniform_stress_60k_4k"] = irregular_stress(ag, torch, dev, stream, n, reps)
+        torch.cuda.empty_cache()
     return res
 
 
@@ -624,18 +776,21 @@ def irregular_stress(ag, torch, dev, stream, n, reps, stripes=1 << 18):
     rr = r.shifted(base)
     log = torch.empty(ag.LOG_BYTES, dtype=torch.uint8, device=dev)
     row = {"ranges": int(len(rr.base))}
-    for label, lg in (("unguarded", None), ("guarded_4KiB", 12), ("guarded_64KiB", 16)):
+    for label, lg in (("unguarded", None), ("guarded_auto", 0), ("guarded_4KiB", 12),
+                      ("guarded_64KiB", 16)):
         dtab = None
-        if lg:
+        if lg is not None:
             t = ag.agile_guard_table_build(rr.base, rr.size, rr.kind, rr.ident, lg)
+            if lg == 0:
+                row["auto_log2_page"] = t.geometry()[0]
             tb = torch.empty(t.device_bytes(), dtype=torch.uint8, device=dev)
             dtab = t.upload(tb, stream)
 
         def once():
-            if lg:
+            if lg is not None:
                 ag.agile_violation_log_init(log, 0, stream)
             ag.agile_irregular_launch("gather", dtab, idx, base, out_t, n, "poison",
-                                      log if lg else None, stream)
+                                      log if lg is not None else None, stream)
         once()
         torch.cuda.synchronize()
         ts = []
@@ -649,34 +804,34 @@ def irregular_stress(ag, torch, dev, stream, n, reps, stripes=1 << 18):
             ts.append(e0.elapsed_time(e1))
         ms = statistics.median(ts)
         cell = {"ms": ms, "useful_gbs": 16 * n / ms / 1e6}
-        if lg:
+        if lg is not None:
             rc, rec = ag.agile_violation_log_read(log, stream)
             assert rec.count == bad.numel(), (label, rec.count, bad.numel())
             cell["violations"] = rec.count
         row[label] = cell
-    row["guarded_over_unguarded"] = row["unguarded"]["ms"] / min(
-        row["guarded_4KiB"]["ms"], row["guarded_64KiB"]["ms"])
+    row["guarded_over_unguarded"] = row["unguarded"]["ms"] / row["guarded_auto"]["ms"]
     del arena
     torch.cuda.empty_cache()
     return row
 
 
-def serve_sweep(ag, torch, dev, rates=(1e3, 3e3, 1e4, 3e4, 1e5), window_s=0.3):
+def serve_sweep(ag, torch, dev, rates=(1e3, 3e3, 1e4, 3e4, 1e5), window_s=0.3, min_requests=3000):
     """64 clients' validate + guarded-launch requests with Poisson arrivals; 0.5% carry a
     bad pointer. Continuous batching against one request at a time, per arrival rate:
-    p50/p99 arrival-to-completion latency and throughput."""
+    p50/p99 arrival-to-completion latency, its breakdown, and throughput; at the top rate
+    the served bytes per second against the HBM peak and the worker's time per request."""
     from paper_2606_06697_b300.serving import ServedClients, latency_stats, serve
     cs = ServedClients(syn.serve_specs(64), dev)
     out = {}
     for rate in rates:
-        n = int(min(max(rate * window_s, 300), 30000))
+        n = int(min(max(rate * window_s, min_requests), 30000))
         gen = syn.serve_requests(cs.layouts, rate, n)
         bad = sum(g["bad"] is not None for g in gen)
         row = {"requests": n, "bad_pointer_requests": bad}
         for mode, cont in (("continuous", True), ("one_at_a_time", False)):
             cs.reset()
             done, peak = serve(cs, gen, continuous=cont)
-            st = latency_stats(gen, done)
+            st = latency_stats(gen, done, cs)
             assert st["rejected"] == bad, "a bad pointer was not rejected"
             row[mode] = st
         out[f"{int(rate)}_per_s"] = row
@@ -711,11 +866,11 @@ def batch_throughput(ag, torch, dev, stream, sizes=(1 << 20, 1 << 28), reps=None
         for lg, (_, _, dtab) in tabs.items():
             tot = 0.0
             for i in range(nrep + 3):
-                flush.fill_(i & 0xFF)                          # evict the inputs from L2
-                ag.agile_violation_log_init(log, 0, stream)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 with torch.cuda.stream(stream):
+                    flush.fill_(i & 0xFF)                      # evict the inputs from L2, on
+                    ag.agile_violation_log_init(log, 0, stream)  # the check's own stream
                     e0.record(stream)
                     ag.agile_guard_check_batch(dtab, da, dw, n, dv, log, stream)
                     e1.record(stream)
@@ -732,11 +887,11 @@ def batch_throughput(ag, torch, dev, stream, sizes=(1 << 20, 1 << 28), reps=None
         apset = syn.table1_protected()
         tot = 0.0
         for i in range(nrep + 3):
-            flush.fill_(i & 0xFF)
-            ag.agile_violation_log_init(log, 0, stream)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+                ag.agile_violation_log_init(log, 0, stream)
                 e0.record(stream)
                 ag.agile_aperture_check_batch((apset.base, apset.size, apset.kind, apset.ident),
                                               da, dw, n, dv, log, stream)
@@ -769,6 +924,8 @@ def main():
                          "e2e,cpu (the guarded steps always run)")
     ap.add_argument("--irregular-n", type=int, default=1 << 28)
     ap.add_argument("--irregular-stripes", type=int, default=4096)
+    ap.add_argument("--irregular-kinds", default="gather,scatter,hist")
+    ap.add_argument("--irregular-dists", default="uniform,zipf")
     args = ap.parse_args()
     args.legs = {"unguarded", "ptx", "batch", "irregular", "clients", "serving", "e2e", "cpu"} \
         if args.legs == "all" else set(args.legs.split(","))
@@ -786,6 +943,7 @@ def main():
         import paper_2606_06697_b300 as ag
         torch.cuda.set_device(local)
         st = torch.cuda.Stream()
+        torch.cuda.set_stream(st)
         print(json.dumps({"batch_check": batch_throughput(ag, torch, f"cuda:{local}", st,
                                                           sizes=(args.batch_only,), reps=args.steps,
                                                           log2_pages=(args.batch_page,))}))

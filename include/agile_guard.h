@@ -129,6 +129,19 @@ typedef struct {
                                  most 32 KiB); ubits_n + 1 bits, the last always clear  */
     uint32_t ubits_log2;
     uint32_t ubits_n;         /* blocks covering the window                             */
+    const uint32_t *cmap;     /* block class map (device), 2 bits per block of
+                                 C = 2^cmap_log2 bytes from lo, 16 blocks per word, block k
+                                 in bits 2(k mod 16)..+1 of word k / 16:
+                                   1  the block lies inside one user range
+                                   2  no range touches the block
+                                   3  the block lies inside one protected range
+                                   0  anything else (MMIO, several ranges, a boundary)
+                                 C is the smallest power of two >= 256 bytes that keeps the
+                                 map at 2^19 blocks (128 KiB) or fewer; cmap_n + 1 blocks,
+                                 the last always 0. Used by the batch check to decide most
+                                 accesses, denied ones included, from one 2-bit code.   */
+    uint32_t cmap_log2;
+    uint32_t cmap_n;          /* blocks covering the window                             */
 } agile_dev_table_t;
 
 /* Decoded violation log. The first fault is the violating access with the smallest
@@ -156,9 +169,14 @@ typedef struct {
  * non-empty, with base + size <= 2^64 - 1 and a known kind; abutting ranges stay
  * separate (an access across two allocations is a straddle). Errors: OVERLAP,
  * ZERO_SIZE, RANGE_OVERFLOW, BAD_KIND, TOO_LARGE (n > AGILE_MAX_RANGES), NOMEM,
- * INVALID_ARG (NULL with n > 0, or log2_page outside [12, 40]). The page size G is
- * 2^log2_page; it is raised until the page map has at most 2^26 entries. The caller's
- * array is copied; *out is freed with agile_guard_table_destroy. */
+ * INVALID_ARG (NULL with n > 0, or log2_page outside [12, 40] and not AGILE_PAGE_AUTO).
+ * The page size G is 2^log2_page; it is raised until the page map has at most 2^26
+ * entries. AGILE_PAGE_AUTO picks it: the largest page from 2 MiB down to 4 KiB at which
+ * at least 95% of the user bytes lie in pages wholly inside one user range (so the page
+ * map alone decides accesses there), with at most 2^24 pages; else the page size with the
+ * largest such share. agile_guard_table_geometry reports the choice. The caller's array
+ * is copied; *out is freed with agile_guard_table_destroy. */
+#define AGILE_PAGE_AUTO 0u
 AGILE_API int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t log2_page,
                             agile_guard_table_t **out);
 
@@ -267,6 +285,17 @@ AGILE_API int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *d
                         const float *d_c, size_t n, float s, int policy, void *d_log,
                         void *stream);
 
+/* agile_stream_launch at a chosen launch shape, so that the guard's cost can be measured
+ * against the unguarded kernel at the same shape: `units` 16-byte units per lane per warp
+ * tile and `blocks_per_sm` blocks of 512 threads per SM, either (8, 1) or (4, 2).
+ * agile_stream_launch runs guarded kernels at (8, 1) and unguarded ones (tbl == NULL) at
+ * (4, 2); the results are identical at every shape. INVALID_ARG for another shape,
+ * otherwise as agile_stream_launch. (Not in the paper: a measurement aid.) */
+AGILE_API int agile_stream_launch_shape(int op, const agile_dev_table_t *tbl, float *d_a,
+                                        const float *d_b, const float *d_c, size_t n, float s,
+                                        int policy, void *d_log, int units, int blocks_per_sm,
+                                        void *stream);
+
 /* agile_stream_launch over host arrays: the inputs come from host memory and the result
  * goes back to it, with the copies inside the call. The n elements are cut into chunks of
  * chunk_elems (a multiple of 4; 0 picks 2^24). Chunk k runs on one of three internal
@@ -278,7 +307,11 @@ AGILE_API int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *d
  * and the log match it exactly. The device arrays are the ones the table guards. Pinned
  * host memory is needed for the copies to overlap. Ordered after earlier work on `stream`;
  * later work on `stream` waits for the whole call. Errors as agile_stream_launch, plus
- * INVALID_ARG for chunk_elems not a multiple of 4. */
+ * INVALID_ARG for chunk_elems not a multiple of 4. Arguments are checked before anything
+ * is queued, so a rejected call queues nothing; a CUDA failure part-way returns
+ * AGILE_ERR_CUDA after making `stream` wait for the chunks already queued, so buffers
+ * may be reused once `stream` has been synchronized. The three streams and four events
+ * are created on the first call per device and calling thread and kept until exit. */
 AGILE_API int agile_stream_launch_host(int op, const agile_dev_table_t *tbl, float *d_a,
                                        float *d_b, float *d_c, float *h_a, const float *h_b,
                                        const float *h_c, size_t n, float s, int policy,
@@ -301,6 +334,19 @@ enum { AGILE_IRR_GATHER = 0, AGILE_IRR_SCATTER = 1, AGILE_IRR_HIST = 2 };
 AGILE_API int agile_irregular_launch(int kind, const agile_dev_table_t *tbl, const int64_t *d_idx,
                                      void *d_base, float *d_out, size_t n, int policy,
                                      void *d_log, void *stream);
+
+/* How a guarded irregular kernel reads the all-user bitmap for its per-lane element
+ * accesses: AGILE_FAST_BITMAP, each lane reads its own word (what agile_irregular_launch
+ * does); AGILE_FAST_MATCH, lanes whose elements fall in the same bitmap block are grouped
+ * with __match_any_sync, the group's leader reads the word and __shfl_sync hands it on.
+ * Both give identical results and logs. (Not in the paper: kept so the two warp-level
+ * fast paths can be measured against each other.) AGILE_FAST_MATCH needs a table and the
+ * POISON policy, INVALID_ARG otherwise; other arguments as agile_irregular_launch. */
+enum { AGILE_FAST_BITMAP = 0, AGILE_FAST_MATCH = 1 };
+AGILE_API int agile_irregular_launch_fastpath(int kind, const agile_dev_table_t *tbl,
+                                              const int64_t *d_idx, void *d_base, float *d_out,
+                                              size_t n, int policy, void *d_log, int fast_path,
+                                              void *stream);
 
 /* ---------------------------------------------------------------- batched clients */
 
@@ -426,7 +472,12 @@ typedef struct {
     uint32_t bad_arg;                   /* first denied argument (rejections)                */
     uint32_t verdict;                   /* its verdict                                       */
     uint32_t launch;                    /* sequence number of the launch that ran it         */
-    uint64_t arrival_ns, admit_ns, done_ns;
+    uint64_t arrival_ns;                /* worker clock: arrival time given with the request  */
+    uint64_t admit_ns;                  /* packed into a launch                              */
+    uint64_t done_ns;                   /* completed: its kernel's last tile done (the
+                                           launch's completion notice), or rejected          */
+    uint64_t seen_ns;                   /* taken up and validated by the worker              */
+    uint64_t queued_ns;                 /* its launch's copy and kernel queued on the stream  */
 } agile_completion_t;
 
 typedef struct {
@@ -459,7 +510,10 @@ AGILE_API int agile_worker_create(const agile_worker_config_t *cfg,
  * passes its arrival time: validated (a denied argument completes it at once with
  * AGILE_VIOLATION), then admitted in arrival order when the memory budget, a launch slot
  * and its exclusive key allow; admitted requests are packed into the next persistent
- * launch while earlier launches still run (continuous batching). */
+ * launch while earlier launches still run (continuous batching). Each request completes
+ * on its own: the launch raises a per-request notice in host-mapped memory when the
+ * request's last tile is done, and the worker then completes it and returns its memory
+ * to the budget, while the rest of that launch may still run. */
 AGILE_API int agile_worker_submit(agile_worker_t *w, const agile_request_t *reqs, size_t n);
 AGILE_API int agile_worker_start(agile_worker_t *w);
 

@@ -13,6 +13,7 @@ from .abi import (  # noqa: F401
     AgileError, DevTable, Module, Table, ViolationRecord, agile_free, agile_guard_check_batch,
     agile_aperture_check_batch, agile_stream_launch_host, agile_selftest_bounded_waits,
     agile_guard_instrument_ptx, agile_guard_table_build, agile_irregular_launch, agile_module_bind, agile_module_launch,
+    agile_irregular_launch_fastpath, agile_stream_launch_shape, FAST_PATHS,
     agile_module_load, agile_module_unload, agile_stream_launch, agile_strerror,
     agile_validate_args, agile_validate_dma, agile_version, agile_violation_log_init, agile_violation_log_read, lib,
     library_path, LOG_BYTES, NO_RANGE, VERDICTS, KINDS, POLICIES, OPS, IRREGULAR)

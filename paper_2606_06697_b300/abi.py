@@ -45,7 +45,9 @@ class _DevTable(ctypes.Structure):
                 ("bytes", ctypes.c_uint64), ("search_steps", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("crange", ctypes.c_void_p),
                 ("remap_or", ctypes.c_uint64), ("ubits", ctypes.c_void_p),
-                ("ubits_log2", ctypes.c_uint32), ("ubits_n", ctypes.c_uint32)]
+                ("ubits_log2", ctypes.c_uint32), ("ubits_n", ctypes.c_uint32),
+                ("cmap", ctypes.c_void_p), ("cmap_log2", ctypes.c_uint32),
+                ("cmap_n", ctypes.c_uint32)]
 
 
 class _Record(ctypes.Structure):
@@ -86,7 +88,8 @@ class Completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("bad_arg", ctypes.c_uint32),
                 ("verdict", ctypes.c_uint32), ("launch", ctypes.c_uint32),
                 ("arrival_ns", ctypes.c_uint64), ("admit_ns", ctypes.c_uint64),
-                ("done_ns", ctypes.c_uint64)]
+                ("done_ns", ctypes.c_uint64), ("seen_ns", ctypes.c_uint64),
+                ("queued_ns", ctypes.c_uint64)]
 
 
 class WorkerConfig(ctypes.Structure):
@@ -123,8 +126,13 @@ _SIG = {
                                                   _P, _P, _P]),
     "agile_stream_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
                                            ctypes.c_float, ctypes.c_int, _P, _P]),
+    "agile_stream_launch_shape": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
+                                                 ctypes.c_float, ctypes.c_int, _P, ctypes.c_int,
+                                                 ctypes.c_int, _P]),
     "agile_irregular_launch": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
                                               ctypes.c_int, _P, _P]),
+    "agile_irregular_launch_fastpath": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t,
+                                                       ctypes.c_int, _P, ctypes.c_int, _P]),
     "agile_stream_launch_host": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                                 ctypes.c_size_t, ctypes.c_float, ctypes.c_int, _P,
                                                 ctypes.c_size_t, _P]),
@@ -388,6 +396,15 @@ def agile_stream_launch(op: str, dev: DevTable | None, d_a, d_b, d_c, n: int, s:
                                      _stream(stream)), "agile_stream_launch")
 
 
+def agile_stream_launch_shape(op: str, dev: DevTable | None, d_a, d_b, d_c, n: int, s: float,
+                              policy: str, d_log, units: int, blocks_per_sm: int,
+                              stream=None) -> None:
+    _check(lib().agile_stream_launch_shape(OPS[op], dev.ref if dev is not None else None,
+                                           _dptr(d_a), _dptr(d_b), _dptr(d_c), n, s,
+                                           POLICIES[policy], _dptr(d_log), units, blocks_per_sm,
+                                           _stream(stream)), "agile_stream_launch_shape")
+
+
 def agile_stream_launch_host(op: str, dev: DevTable | None, d_a, d_b, d_c, h_a, h_b, h_c, n: int,
                              s: float = 3.0, policy: str = "poison", d_log=None,
                              chunk_elems: int = 0, stream=None) -> None:
@@ -405,6 +422,19 @@ def agile_irregular_launch(kind: str, dev: DevTable | None, d_idx, d_base, d_out
                                         _dptr(d_idx), _dptr(d_base), _dptr(d_out), n,
                                         POLICIES[policy], _dptr(d_log), _stream(stream)),
            "agile_irregular_launch")
+
+
+FAST_PATHS = {"bitmap": 0, "match": 1}
+
+
+def agile_irregular_launch_fastpath(kind: str, dev: DevTable | None, d_idx, d_base, d_out, n: int,
+                                    policy: str = "poison", d_log=None, fast_path: str = "bitmap",
+                                    stream=None) -> None:
+    _check(lib().agile_irregular_launch_fastpath(IRREGULAR[kind], dev.ref if dev is not None else None,
+                                                 _dptr(d_idx), _dptr(d_base), _dptr(d_out), n,
+                                                 POLICIES[policy], _dptr(d_log),
+                                                 FAST_PATHS[fast_path], _stream(stream)),
+           "agile_irregular_launch_fastpath")
 
 
 # ---------------------------------------------------------------- batched clients

@@ -25,9 +25,22 @@ struct agile_guard_table {
     size_t off_ubits = 0;
     uint32_t ubits_log2 = 12;
     uint32_t ubits_n = 0;
+    size_t off_cmap = 0;                  // block class map (2 bits per block)
+    uint32_t cmap_log2 = 8;
+    uint32_t cmap_n = 0;
 };
 
 namespace agile {
+
+// Byte layout at the start of an uploaded table's device buffer: the agile_dev_table_t
+// header, the 64-byte zero page, the 64-byte sink page, then the page map.
+constexpr size_t kTableHeaderBytes = 256, kTableZeroOff = 256, kTableSinkOff = 320,
+                 kTablePageOff = 384;
+
+// Device address of the buffer that holds an uploaded table, where its header lives.
+inline const unsigned char *table_buffer(const agile_dev_table_t &T) {
+    return reinterpret_cast<const unsigned char *>(T.page) - kTablePageOff;
+}
 
 // Host form of the rule (same two-level lookup as the device), used by
 // agile_validate_args and by the serving loop's admission checks.

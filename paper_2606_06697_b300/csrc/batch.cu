@@ -6,7 +6,9 @@
 // the table page size.
 //
 // Device buffer (caller-owned, agile_batch_device_bytes):
-//   [0, 64)        header: item count, tile count, tile claim counter, tile size
+//   [0, 64)        header: item count, tile count, tile claim counter, tile size, and for a
+//                  launch that reports each item's completion, the addresses of the
+//                  per-item done counters and of the per-item notice flags
 //   [64, ...)      n work items, 64 bytes each
 //   then           n + 1 u64 tile prefix sums (tiles of item i are prefix[i] .. prefix[i+1])
 // Blocks claim tiles with one atomic on the counter; the launch resets it first.
@@ -46,7 +48,10 @@ struct BatchHdr {
     unsigned long long counter;
     uint32_t tile;
     uint32_t pad;
-    unsigned long long reserved[4];
+    unsigned int *done;            // per-item count of finished tiles (zeroed), or NULL
+    unsigned int *notice;          // per-item flag set to 1 when the item's last tile is done,
+                                   // in host-mapped memory, or NULL for no notices
+    unsigned long long reserved[2];
 };
 static_assert(sizeof(BatchHdr) == 64, "header");
 static_assert(sizeof(agile_work_t) == 64, "work item");
@@ -145,6 +150,18 @@ k_batch(BatchHdr *H, const agile_work_t *__restrict__ items, const uint64_t *__r
         agile::slots_flush(static_cast<LogDev *>(W.log), S);   // one update per tile
         agile::slots_init(S);
         __syncthreads();
+        // Completion notice: the block that finishes an item's last tile tells the host,
+        // so a caller can complete that item without waiting for the whole launch. The
+        // barrier above orders the tile's writes and log updates before this thread's
+        // fence; the count then orders every tile before the notice.
+        if (threadIdx.x == 0 && H->notice != nullptr) {
+            __threadfence();
+            const unsigned int tiles = (unsigned int)(prefix[s_item + 1] - prefix[s_item]);
+            if (atomicAdd(&H->done[s_item], 1u) + 1u == tiles) {
+                __threadfence_system();
+                *(volatile unsigned int *)(H->notice + s_item) = 1u;
+            }
+        }
     }
 }
 

@@ -3,14 +3,20 @@
 // and the violation count in the log.
 //
 // Launch shape: one 1024-thread block per SM, a warp-uniform grid-stride loop. Each lane
-// takes 8 consecutive accesses per round: four 16-byte address loads, one 8-byte width
-// load, one 8-byte verdict store. Staged into shared memory by bulk copies: the page map,
-// the packed range records (windows under 4 GiB; otherwise the range arrays) and the
-// all-user block bitmap. Pass 1 decides the accesses inside all-user blocks from the
-// bitmap, without branches; pass 2 deals the warp's remaining accesses out over its lanes
-// and decides each by the full rule (the 32-bit uniform decision over the packed records
-// where it applies). Each thread keeps its smallest violation in registers; the block
-// reduces them once at the end.
+// takes kG groups of 8 consecutive accesses per round (four 16-byte address loads, one
+// 8-byte width load, one 8-byte verdict store per group). Staged into shared memory by
+// bulk copies: the block class map (2 bits per block of 256 B or more) and, where they
+// fit beside it, the page map and the packed range records (windows under 4 GiB) or the
+// range arrays.
+//
+// Pass 1 decides each access from its block's 2-bit class alone, without branches: an
+// access inside one block of class user, hole or protected gets ALLOW, UNMAPPED or
+// PROTECTED. The rest -- blocks holding a boundary, MMIO blocks, accesses that cross a
+// block edge or lie outside the window, illegal widths -- are "open". Pass 2 deals the
+// warp's open accesses out over its lanes, 32 at a time, and decides each by the full
+// rule (the 32-bit uniform decision over the packed records where it applies). Each
+// thread keeps its smallest violation in registers; the block reduces them once at the
+// end.
 #include <cuda_runtime.h>
 
 #include "agile_internal.h"
@@ -22,8 +28,11 @@ using agile::LaneLog;
 using agile::LogDev;
 using agile::TView;
 
-constexpr int kThreads = 1024;   // one block per SM: 250 G checks/s at 2^28 against 231
-                                 // for 2 x 512 and 218 for 4 x 256 (same code otherwise)
+constexpr int kThreads = 1024;   // one block per SM
+
+// Dynamic shared memory a launch may stage (the static part -- mbarrier, log reduction --
+// takes about 1 KB of the 227 KB an SM gives one block).
+constexpr uint64_t kStageBudget = 224 * 1024;
 
 // Uniform decision in 32-bit arithmetic, for tables whose window spans under 4 GiB (the
 // packed records hold each range's start and last byte as offsets from the window start,
@@ -83,33 +92,60 @@ __device__ __forceinline__ bool decide32(const TView &V, uint64_t a, uint32_t w,
     return true;
 }
 
-// The bitmap test of pass 1 for windows under 4 GiB (the packed-record tables): one 64-bit
-// window check, then 32-bit arithmetic (blocks there are at most 2^14 bytes).
-__device__ __forceinline__ bool user_fast32(const TView &V, uint64_t a, uint32_t w) {
-    const uint64_t off = a - V.lo;
-    const uint32_t o = (uint32_t)off;
-    const uint32_t k = off <= V.last - V.lo ? o >> V.ulg : V.un;   // outside: the clear bit
-    const uint32_t m = (1u << V.ulg) - 1u;
-    return ((V.ubits[k >> 5] >> (k & 31)) & 1u) && (o & m) + w <= m + 1u;
+// x >> s with the PTX rule for shift counts of 32 and more (the result is 0).
+__device__ __forceinline__ uint32_t shr_clamped(uint32_t x, uint32_t s) {
+    uint32_t r;
+    asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
+    return r;
 }
 
 __device__ __forceinline__ bool legal_width(uint32_t w) {
-    return w <= 16 && ((0x10116u >> w) & 1u);        // 1, 2, 4, 8, 16
+    return shr_clamped(0x10116u, w) & 1u;             // 1, 2, 4, 8, 16
 }
 
-// Full rule for one access (for the accesses the uniform decision leaves open).
+// Pass-1 class of one access from the block class map: the 2-bit code of its block (1
+// user, 2 hole, 3 protected) when the access is decided here -- it lies inside that block,
+// inside the window, and has a legal width -- else 0 ("open": the block holds a boundary
+// or MMIO, the access crosses the block's end, lies outside the window, or has an illegal
+// width). C32: the window spans under 4 GiB, so block index and offset are 32-bit.
 template <bool C32>
-__device__ __forceinline__ uint32_t full_one(const TView &V, uint64_t a, uint32_t w, size_t i,
-                                             LaneLog &ll) {
-    uint32_t rid = agile::kNoRange, v;
-    if (!legal_width(w)) v = AGILE_DENY_INVALID;
-    else if constexpr (C32) v = agile::classify_slow(V, a, w, &rid);
-    else v = agile::classify(V, a, w, &rid);
-    if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
-    return v;
+__device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32_t w) {
+    const uint64_t off = a - V.lo;
+    uint32_t blk;
+    bool ok;
+    if constexpr (C32) {
+        const uint32_t o = (uint32_t)off;
+        const uint32_t k = o >> V.clg;
+        blk = k < V.cn ? k : V.cn;                     // past the window: the open entry
+        const uint32_t m = (1u << V.clg) - 1u;
+        ok = (off >> 32) == 0 && (o & m) + w <= m + 1u;
+    } else {
+        const uint64_t k = off >> V.clg;
+        blk = k < V.cn ? (uint32_t)k : V.cn;
+        const uint64_t m = (1ull << V.clg) - 1;
+        ok = (off & m) + w <= m + 1;
+    }
+    // 16 codes per word: rotating the word by 2 * blk (mod 32) brings this block's to bit 0
+    const uint32_t word = V.cmap[blk >> 4];
+    const uint32_t code = __funnelshift_r(word, word, blk * 2u) & 3u;
+    return ok && legal_width(w) ? code : 0u;
 }
 
-template <int MODE, int VEC, int kG>
+// Full rule for one access (pass 2, the n mod 8 tail, and the misaligned form).
+template <bool C32>
+__device__ __forceinline__ uint32_t full_rule(const TView &V, uint64_t a, uint32_t w, uint32_t *rid) {
+    *rid = agile::kNoRange;
+    if (!legal_width(w) || a > ~0ull - w) return AGILE_DENY_INVALID;
+    uint32_t v;
+    if constexpr (C32) {
+        if (decide32(V, a, w, &v, rid)) return v;
+        return agile::classify_slow(V, a, w, rid);
+    } else {
+        return agile::classify(V, a, w, rid);
+    }
+}
+
+template <int MODE, bool C32, int kG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
               const uint8_t *__restrict__ width, uint8_t *__restrict__ verdict, size_t n,
@@ -120,138 +156,181 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
 
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
-    const size_t ngroups = n / VEC;
+    const size_t ngroups = n / 8;
+    const uint32_t lane = threadIdx.x & 31;
+    LaneLog ll;                        // pass-2 violations: count and smallest record
+    uint32_t cnt1 = 0;                 // pass-1 denials
+    size_t first1 = ~(size_t)0;        // this lane's first pass-1 denial (its smallest)
 
-    constexpr bool kC32 = (MODE & agile::ST_COMPACT) != 0;
-    LaneLog ll;
-    if constexpr (VEC == 8) {
-        // Each lane takes kG groups of 8 accesses per round (groups g0 + 32h + lane,
-        // coalesced across the warp). With kG = 2 pass 2 has twice the open accesses to
-        // deal out and its 32-lane rounds run fuller (268 -> 285 G checks/s at 2^28);
-        // batches too small to give every lane two groups use kG = 1.
-        const uint32_t lane = threadIdx.x & 31;
-        for (size_t g0 = (tid - lane) * kG; g0 < ngroups; g0 += nthreads * kG) {   // warp-uniform
-            // Pass 1, branch-free: an access inside an all-user block of the bitmap is
-            // allowed. The others ("open") are decided in pass 2.
-            uint32_t open = 0;
+    // Groups g0 + 32h + lane (h < kG), coalesced across the warp.
+    for (size_t g0 = (tid - lane) * kG; g0 < ngroups; g0 += nthreads * kG) {   // warp-uniform
+        uint32_t open = 0;             // bit 4k + h: access k of group h not decided in pass 1
 #pragma unroll
-            for (int h = 0; h < kG; ++h) {
-                const size_t g = g0 + 32 * h + lane;
-                if (g >= ngroups) continue;
-                // Default-cached loads: pass 2 re-reads its accesses, which then hit L1 (with
-                // streaming loads they came from DRAM again, 40% more read traffic).
-                const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
-                uint64_t av[8];
+        for (int h = 0; h < kG; ++h) {
+            const size_t g = g0 + 32 * h + lane;
+            if (g >= ngroups) continue;
+            // Default-cached loads: pass 2 re-reads its open accesses from L1 or L2.
+            const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
+            uint64_t av[8];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {          // registers only: no indexed arrays
-                    const uint4 q = __ldg(pa + k);
-                    av[2 * k] = (uint64_t)q.y << 32 | q.x;
-                    av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
-                }
-                const uint64_t wv = __ldg(reinterpret_cast<const unsigned long long *>(width + g * 8));
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t w = (uint32_t)(wv >> (8 * k)) & 0xFFu;
-                    bool inb;
-                    if constexpr (kC32) inb = user_fast32(V, av[k], w);
-                    else inb = agile::block_user_fast(V, av[k], w, agile::user_bits(V, av[k]));
-                    const bool ok = legal_width(w) && av[k] <= ~0ull - w && inb;
-                    open |= (uint32_t)!ok << (8 * h + k);
-                }
-                __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), 0ull);
+            for (int k = 0; k < 4; ++k) {              // registers only: no indexed arrays
+                const uint4 q = __ldg(pa + k);
+                av[2 * k] = (uint64_t)q.y << 32 | q.x;
+                av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
             }
-            // Pass 2: the warp's open accesses are dealt out to its lanes, 32 at a time, so
-            // the full decision runs ceil(open / 32) times per warp rather than once for
-            // every position any lane has open.
-            const uint32_t c = __popc(open);
-            uint32_t incl = c;
+            const uint64_t wv = __ldg(reinterpret_cast<const unsigned long long *>(width + g * 8));
+            // The eight codes, access k's in nibble k. A byte permute turns four nibbles into
+            // four verdict bytes at once: code c selects byte c of 0x01040000, so 0 (open)
+            // and 1 (user) give ALLOW, 2 (hole) UNMAPPED, 3 (protected) PROTECTED.
+            uint32_t sel = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(agile::kFull, incl, o);
-                if (lane >= (uint32_t)o) incl += t;
+            for (int k = 0; k < 8; ++k)
+                sel += cmap_code<C32>(V, av[k], (uint32_t)(wv >> (8 * k)) & 0xFFu) << (4 * k);
+            const uint32_t vlo = __byte_perm(0x01040000u, 0u, sel);
+            const uint32_t vhi = __byte_perm(0x01040000u, 0u, sel >> 16);
+            __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8),
+                   (unsigned long long)vhi << 32 | vlo);
+            const uint32_t nz = (sel | (sel >> 1)) & 0x11111111u;   // nibble k: access k decided
+            open |= (~nz & 0x11111111u) << h;
+            const uint32_t dn = (sel >> 1) & 0x11111111u;           // decided denials (codes 2, 3)
+            cnt1 += __popc(dn);
+            if (dn != 0 && first1 == ~(size_t)0) first1 = g * 8 + ((__ffs(dn) - 1) >> 2);
+        }
+        // Pass 2: the warp's open accesses are dealt out to its lanes, 32 at a time, so
+        // the full decision runs ceil(open / 32) times per warp rather than once for
+        // every position any lane has open.
+        const uint32_t c = __popc(open);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(agile::kFull, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(agile::kFull, incl, 31);
+        const uint32_t excl = incl - c;
+        __syncwarp();                                  // the pass-1 stores above come first
+        for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            uint32_t own = 0;                          // lanes whose open accesses all precede q
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                const uint32_t t = __shfl_sync(agile::kFull, incl, own + step - 1);
+                own = t <= q ? own + step : own;
             }
-            const uint32_t total = __shfl_sync(agile::kFull, incl, 31);
-            const uint32_t excl = incl - c;
-            __syncwarp();                              // the zero stores above come first
-            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-                const uint32_t q = q0 + lane;
-                uint32_t own = 0;                      // lanes whose open accesses all precede q
-#pragma unroll
-                for (int step = 16; step; step >>= 1) {
-                    const uint32_t t = __shfl_sync(agile::kFull, incl, own + step - 1);
-                    own = t <= q ? own + step : own;
-                }
-                const uint32_t omask = __shfl_sync(agile::kFull, open, own & 31);
-                const uint32_t oexcl = __shfl_sync(agile::kFull, excl, own & 31);
-                if (q < total) {
-                    uint32_t m = omask;
-                    for (uint32_t r = q - oexcl; r; --r) m &= m - 1;   // drop the earlier ones
-                    const int b = __ffs(m) - 1;                       // bit 8h + k
-                    const size_t i = (g0 + 32 * (b >> 3) + own) * 8 + (b & 7);
-                    const uint64_t a = addr[i];
-                    const uint32_t w = width[i];
-                    uint32_t v = 0, rid = agile::kNoRange;
-                    bool done = false;
-                    if constexpr (kC32) done = legal_width(w) && a <= ~0ull - w && decide32(V, a, w, &v, &rid);
-                    if (!done) v = full_one<kC32>(V, a, w, i, ll);
-                    else if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
-                    if (v != AGILE_ALLOW) verdict[i] = (uint8_t)v;
+            const uint32_t omask = __shfl_sync(agile::kFull, open, own & 31);
+            const uint32_t oexcl = __shfl_sync(agile::kFull, excl, own & 31);
+            if (q < total) {
+                uint32_t m = omask;
+                for (uint32_t r = q - oexcl; r; --r) m &= m - 1;   // drop the earlier ones
+                const int b = __ffs(m) - 1;                       // bit 4k + h
+                const size_t i = (g0 + 32 * (b & 3) + own) * 8 + (b >> 2);
+                const uint64_t a = addr[i];
+                const uint32_t w = width[i];
+                uint32_t rid;
+                const uint32_t v = full_rule<C32>(V, a, w, &rid);
+                if (v != AGILE_ALLOW) {
+                    ll.note(i, agile::pack_info(0, v, w, rid), a);
+                    verdict[i] = (uint8_t)v;
                 }
             }
         }
-    } else {
-        for (size_t g = tid; g < ngroups; g += nthreads)
-            verdict[g] = (uint8_t)full_one<kC32>(V, addr[g], width[g], g, ll);
     }
-    if (VEC > 1 && blockIdx.x == 0 && threadIdx.x < 32) {    // the last n % VEC accesses
-        const size_t i = ngroups * VEC + threadIdx.x;
-        if (i < n) verdict[i] = (uint8_t)full_one<kC32>(V, addr[i], width[i], i, ll);
+    if (blockIdx.x == 0 && threadIdx.x < 32) {        // the last n % 8 accesses
+        const size_t i = ngroups * 8 + threadIdx.x;
+        if (i < n) {
+            const uint64_t a = addr[i];
+            const uint32_t w = width[i];
+            uint32_t rid;
+            const uint32_t v = full_rule<C32>(V, a, w, &rid);
+            if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
+            verdict[i] = (uint8_t)v;
+        }
+    }
+    // The record of this lane's first pass-1 denial: its range id comes from the full rule.
+    if (first1 != ~(size_t)0) {
+        const uint64_t a = addr[first1];
+        const uint32_t w = width[first1];
+        uint32_t rid;
+        const uint32_t v = full_rule<C32>(V, a, w, &rid);
+        if (ll.cnt == 0 || first1 < ll.key) {
+            ll.key = first1;
+            ll.info = agile::pack_info(0, v, w, rid);
+            ll.addr = a;
+        }
+    }
+    ll.cnt += cnt1;
+    agile::block_log_flush(log, ll);
+}
+
+// Inputs not aligned for vector loads: one access per thread per step, full rule.
+template <int MODE, bool C32>
+__global__ void __launch_bounds__(kThreads, 1)
+k_check_batch_scalar(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
+                     const uint8_t *__restrict__ width, uint8_t *__restrict__ verdict, size_t n,
+                     LogDev *log) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_bar;
+    const TView V = agile::stage_table<MODE>(T, smem, &s_bar, log);
+    LaneLog ll;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const uint64_t a = addr[i];
+        const uint32_t w = width[i];
+        uint32_t rid;
+        const uint32_t v = full_rule<C32>(V, a, w, &rid);
+        if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
+        verdict[i] = (uint8_t)v;
     }
     agile::block_log_flush(log, ll);
 }
 
-template <int MODE, int VEC, int kG>
-int launch_g(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
-             uint8_t *v, LogDev *log, cudaStream_t st, uint32_t smem, unsigned blocks) {
-    if (smem > 48 * 1024) {
-        AGILE_CUDA_TRY(cudaFuncSetAttribute(k_check_batch<MODE, VEC, kG>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
-    k_check_batch<MODE, VEC, kG><<<blocks, kThreads, smem, st>>>(T, a, w, v, n, log);
+template <typename K>
+int launch_kernel(K kernel, const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w,
+                  size_t n, uint8_t *v, LogDev *log, cudaStream_t st, uint32_t smem, unsigned blocks) {
+    if (smem > 48 * 1024)
+        AGILE_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kernel<<<blocks, kThreads, smem, st>>>(T, a, w, v, n, log);
     AGILE_CUDA_TRY(cudaGetLastError());
     return AGILE_OK;
 }
 
-template <int MODE, int VEC>
+template <int MODE, bool C32>
 int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
-           uint8_t *v, LogDev *log, cudaStream_t st) {
-    const uint32_t smem = agile::stage_bytes(T, MODE);
-    size_t groups = n / VEC;
-    size_t want = (groups + kThreads - 1) / kThreads;
-    size_t cap = (size_t)agile::sm_count();
-    unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
-    if (VEC == 8 && groups >= 2 * (size_t)blocks * kThreads)
-        return launch_g<MODE, VEC, 2>(T, a, w, n, v, log, st, smem, blocks);
-    return launch_g<MODE, VEC, 1>(T, a, w, n, v, log, st, smem, blocks);
+           uint8_t *v, LogDev *log, cudaStream_t st, bool vec) {
+    const size_t units = vec ? n / 8 : n;
+    const size_t want = (units + kThreads - 1) / kThreads;
+    const size_t cap = (size_t)agile::sm_count();
+    const unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
+    if (!vec) {                                        // the class map serves pass 1 only
+        constexpr int kM = MODE & ~agile::ST_CMAP;
+        return launch_kernel(k_check_batch_scalar<kM, C32>, T, a, w, n, v, log, st,
+                             (uint32_t)agile::stage_bytes(T, kM), blocks);
+    }
+    const uint32_t smem = (uint32_t)agile::stage_bytes(T, MODE);
+    // Four (else two) groups per lane per round when the batch gives every lane that many:
+    // pass 2 then deals out more open accesses per round and its rounds run fuller.
+    if (units >= 4 * (size_t)blocks * kThreads)
+        return launch_kernel(k_check_batch<MODE, C32, 4>, T, a, w, n, v, log, st, smem, blocks);
+    if (units >= 2 * (size_t)blocks * kThreads)
+        return launch_kernel(k_check_batch<MODE, C32, 2>, T, a, w, n, v, log, st, smem, blocks);
+    return launch_kernel(k_check_batch<MODE, C32, 1>, T, a, w, n, v, log, st, smem, blocks);
 }
 
-template <int VEC>
-int launch_mode(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
-                uint8_t *v, LogDev *log, cudaStream_t st) {
-    constexpr int kCB = agile::STAGE_COMPACT | agile::ST_BITS, kAB = agile::STAGE_ALL | agile::ST_BITS;
-    constexpr int kPB = agile::STAGE_PAGES | agile::ST_BITS;
-    // The bitmap is staged at every size: without it, pass 1 reads it through L1 and the
-    // 2^20-access check takes 18.4 us instead of 16.4.
-    switch (agile::stage_mode(T, true, true, true)) {
-        case kCB: return launch<kCB, VEC>(T, a, w, n, v, log, st);
-        case agile::STAGE_COMPACT: return launch<agile::STAGE_COMPACT, VEC>(T, a, w, n, v, log, st);
-        case kAB: return launch<kAB, VEC>(T, a, w, n, v, log, st);
-        case agile::STAGE_ALL: return launch<agile::STAGE_ALL, VEC>(T, a, w, n, v, log, st);
-        case kPB: return launch<kPB, VEC>(T, a, w, n, v, log, st);
-        case agile::STAGE_PAGES: return launch<agile::STAGE_PAGES, VEC>(T, a, w, n, v, log, st);
-        case agile::STAGE_BITS: return launch<agile::STAGE_BITS, VEC>(T, a, w, n, v, log, st);
-        default: return launch<agile::STAGE_NONE, VEC>(T, a, w, n, v, log, st);
-    }
+// Staging: the class map always (at most 128 KiB + 4 bytes); beside it, whatever fits the
+// budget of the page map and the packed records (windows under 4 GiB) or the range
+// arrays, in that order of preference. Sections left out are read through L1.
+template <bool C32>
+int launch_staged(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
+                  uint8_t *v, LogDev *log, cudaStream_t st, bool vec) {
+    using namespace agile;
+    constexpr int kMPC = ST_CMAP | ST_PAGES | ST_COMPACT, kMC = ST_CMAP | ST_COMPACT;
+    constexpr int kMA = ST_CMAP | STAGE_ALL, kMP = ST_CMAP | ST_PAGES;
+    if (T.npages == 0) return launch<STAGE_NONE, false>(T, a, w, n, v, log, st, vec);
+    if (C32 && stage_bytes(T, kMPC) <= kStageBudget) return launch<kMPC, C32>(T, a, w, n, v, log, st, vec);
+    if (C32 && stage_bytes(T, kMC) <= kStageBudget) return launch<kMC, C32>(T, a, w, n, v, log, st, vec);
+    if (stage_bytes(T, kMA) <= kStageBudget) return launch<kMA, C32>(T, a, w, n, v, log, st, vec);
+    if (stage_bytes(T, kMP) <= kStageBudget) return launch<kMP, C32>(T, a, w, n, v, log, st, vec);
+    return launch<ST_CMAP, C32>(T, a, w, n, v, log, st, vec);
 }
 
 }  // namespace
@@ -263,10 +342,11 @@ extern "C" int agile_guard_check_batch(const agile_dev_table_t *tbl, const uint6
     if (n == 0) return AGILE_OK;
     if (d_addr == nullptr || d_width == nullptr || d_verdict == nullptr) return AGILE_ERR_INVALID_ARG;
     if (d_log != nullptr && ((uintptr_t)d_log & 15) != 0) return AGILE_ERR_ALIGN;
+    if (tbl->cmap == nullptr) return AGILE_ERR_INVALID_ARG;
     const bool vec = ((uintptr_t)d_addr & 15) == 0 && ((uintptr_t)d_width & 7) == 0 &&
                      ((uintptr_t)d_verdict & 7) == 0;
     LogDev *log = (LogDev *)d_log;
     cudaStream_t st = (cudaStream_t)stream;
-    return vec ? launch_mode<8>(*tbl, d_addr, d_width, n, d_verdict, log, st)
-               : launch_mode<1>(*tbl, d_addr, d_width, n, d_verdict, log, st);
+    return tbl->crange != nullptr ? launch_staged<true>(*tbl, d_addr, d_width, n, d_verdict, log, st, vec)
+                                  : launch_staged<false>(*tbl, d_addr, d_width, n, d_verdict, log, st, vec);
 }

@@ -2,11 +2,12 @@
 // global access; Sec. IV-E: the user / protected / MMIO classification rule).
 //
 // Table layout in device memory (one caller-owned buffer, written by the upload):
-//   [0, 128)    agile_dev_table_t header (absolute device pointers)
-//   [128, 192)  zero page: denied loads under SINK/POISON read these 64 zero bytes
-//   [192, 256)  sink page: denied stores under SINK land here
-//   [256, ...)  page map, npages + 1 u32 entries, padded to 256 bytes
-//   then base[n] u64, end[n] u64, kind[n] u32, id[n] u32 (ascending base), each 256-aligned
+//   [0, 256)    agile_dev_table_t header (absolute device pointers)
+//   [256, 320)  zero page: denied loads under SINK/POISON read these 64 zero bytes
+//   [320, 384)  sink page: denied stores under SINK land here
+//   [384, ...)  page map, npages + 1 u32 entries, padded to 256 bytes
+//   then base[n] u64, end[n] u64, kind[n] u32, id[n] u32 (ascending base), each 256-aligned,
+//   the packed records (windows under 4 GiB), the all-user bitmap and the block class map
 //
 // Two-level lookup. The window [lo, lo + npages*G) is cut into pages of G bytes. Entry p
 // holds in bits 0-29 the index f_p of the first range whose end lies above the page's
@@ -33,11 +34,6 @@ enum : uint32_t { PG_MIXED = 0, PG_USER = 1, PG_HOLE = 2, PG_DENY = 3 };
 constexpr uint32_t kIdxMask = 0x3FFFFFFFu;
 constexpr uint32_t kNoRange = 0xFFFFFFFFu;
 constexpr unsigned kFull = 0xFFFFFFFFu;
-
-constexpr size_t kHeaderBytes = 128;
-constexpr size_t kZeroOff = 128;
-constexpr size_t kSinkOff = 192;
-constexpr size_t kPageOff = 256;
 
 // Device log, AGILE_LOG_BYTES bytes, 16-byte aligned. Two 128-bit words are kept at their
 // lexicographic minimum by compare-and-swap: first = (key, info) and where = (key, addr),
@@ -72,13 +68,16 @@ struct TView {
     const uint4 *crange;        // {start - lo, last - lo, rank, id} (windows under 4 GiB), or NULL
     const uint32_t *ubits;      // all-user block bitmap (un + 1 bits, the last clear)
     uint32_t ulg, un;           // block size 2^ulg, blocks in the window
+    const uint32_t *cmap;       // block class map (2 bits per block, cn + 1 blocks)
+    uint32_t clg, cn;           // block size 2^clg, blocks in the window
 };
 
 __device__ __forceinline__ TView view_of(const agile_dev_table_t &T) {
     const uint64_t G = 1ull << T.log2_page;
     return TView{T.lo, T.npages, G - 1, T.lo + (T.npages << T.log2_page) - 1, T.log2_page, T.n,
                  T.search_steps, T.page, T.base, T.end, T.kind, T.id,
-                 reinterpret_cast<const uint4 *>(T.crange), T.ubits, T.ubits_log2, T.ubits_n};
+                 reinterpret_cast<const uint4 *>(T.crange), T.ubits, T.ubits_log2, T.ubits_n,
+                 T.cmap, T.cmap_log2, T.cmap_n};
 }
 
 __device__ __forceinline__ uint32_t deny_of_kind(uint32_t kind) {
@@ -316,8 +315,9 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
 }
 
 // Shared-memory staging, chosen by the host as a set of sections: the page map, the
-// range arrays, the packed records, the all-user bitmap. Laid out in that order.
-enum : int { ST_PAGES = 1, ST_RANGES = 2, ST_COMPACT = 4, ST_BITS = 8 };
+// range arrays, the packed records, the all-user bitmap, the block class map. Laid out
+// in that order.
+enum : int { ST_PAGES = 1, ST_RANGES = 2, ST_COMPACT = 4, ST_BITS = 8, ST_CMAP = 16 };
 enum : int {
     STAGE_NONE = 0, STAGE_PAGES = ST_PAGES, STAGE_ALL = ST_PAGES | ST_RANGES,
     STAGE_COMPACT = ST_PAGES | ST_COMPACT, STAGE_BITS = ST_BITS
@@ -329,13 +329,19 @@ __host__ __device__ inline uint32_t ubits_bytes(const agile_dev_table_t &T) {
     return round16(((uint64_t)T.ubits_n + 1 + 31) / 32 * 4);
 }
 
-// Bytes of shared memory a staging mode needs for table T.
-__host__ __device__ inline uint32_t stage_bytes(const agile_dev_table_t &T, int mode) {
-    uint32_t b = 0;
-    if (mode & ST_PAGES) b += round16((T.npages + 1) * 4);
+__host__ __device__ inline uint32_t cmap_bytes(const agile_dev_table_t &T) {
+    return round16(((uint64_t)T.cmap_n + 1 + 15) / 16 * 4);
+}
+
+// Bytes of shared memory a staging mode needs for table T (saturating: a map too large
+// for shared memory reports more than any budget).
+__host__ __device__ inline uint64_t stage_bytes(const agile_dev_table_t &T, int mode) {
+    uint64_t b = 0;
+    if (mode & ST_PAGES) b += ((T.npages + 1) * 4 + 15) & ~15ull;
     if (mode & ST_RANGES) b += 2 * round16(T.n * 8ull) + 2 * round16(T.n * 4ull);
     if (mode & ST_COMPACT) b += round16(T.n * 16ull);       // packed records
     if (mode & ST_BITS) b += ubits_bytes(T);
+    if (mode & ST_CMAP) b += cmap_bytes(T);
     return b;
 }
 
@@ -358,12 +364,13 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     TView V = view_of(T);
     if constexpr (MODE == STAGE_NONE) return V;
     constexpr bool kPages = MODE & ST_PAGES, kRanges = MODE & ST_RANGES;
-    constexpr bool kCompact = MODE & ST_COMPACT, kBits = MODE & ST_BITS;
+    constexpr bool kCompact = MODE & ST_COMPACT, kBits = MODE & ST_BITS, kCmap = MODE & ST_CMAP;
     const uint32_t pb = kPages ? round16((T.npages + 1) * 4) : 0;
     const uint32_t bb = round16(T.n * 8ull), kb = round16(T.n * 4ull);
     const uint32_t rb = kRanges ? 2 * bb + 2 * kb : 0;
     const uint32_t cb = kCompact ? round16(T.n * 16ull) : 0;
     const uint32_t ub = kBits ? ubits_bytes(T) : 0;
+    const uint32_t mb = kCmap ? cmap_bytes(T) : 0;
     uint32_t *s_page = reinterpret_cast<uint32_t *>(smem);
     uint64_t *s_base = reinterpret_cast<uint64_t *>(smem + pb);
     uint64_t *s_end = reinterpret_cast<uint64_t *>(smem + pb + bb);
@@ -371,6 +378,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + pb + 2 * bb + kb);
     uint4 *s_cr = reinterpret_cast<uint4 *>(smem + pb + rb);
     uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + pb + rb + cb);
+    uint32_t *s_cmap = reinterpret_cast<uint32_t *>(smem + pb + rb + cb + ub);
     const uint32_t bar = smem_addr(s_bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -378,7 +386,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t total = pb + (T.n > 0 ? rb + cb : 0) + ub;
+        const uint32_t total = pb + (T.n > 0 ? rb + cb : 0) + ub + mb;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total)
                      : "memory");
         if (kPages) bulk_g2s(s_page, T.page, pb, bar);
@@ -390,11 +398,13 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
         }
         if (kCompact && T.n > 0) bulk_g2s(s_cr, T.crange, cb, bar);
         if (kBits) bulk_g2s(s_bits, T.ubits, ub, bar);
+        if (kCmap) bulk_g2s(s_cmap, T.cmap, mb, bar);
     }
     if (!mbar_wait(bar, 0)) {               // (block-uniform only by timing: any thread may)
         if (log != nullptr && threadIdx.x == 0) atomicOr(&log->status, AGILE_LOG_STATUS_TIMEOUT);
         mbar_wait(bar, 0);                  // let copies in flight land, then copy by hand:
-        for (uint32_t i = threadIdx.x; i < pb / 4; i += blockDim.x) s_page[i] = T.page[i];
+        if (kPages)
+            for (uint32_t i = threadIdx.x; i < pb / 4; i += blockDim.x) s_page[i] = T.page[i];
         if (kRanges)                        // identical bytes, so a late bulk write is harmless
             for (uint32_t i = threadIdx.x; i < T.n; i += blockDim.x) {
                 s_base[i] = T.base[i]; s_end[i] = T.end[i]; s_kind[i] = T.kind[i]; s_id[i] = T.id[i];
@@ -402,7 +412,10 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
         if (kCompact)
             for (uint32_t i = threadIdx.x; i < T.n; i += blockDim.x)
                 s_cr[i] = reinterpret_cast<const uint4 *>(T.crange)[i];
-        for (uint32_t i = threadIdx.x; i < ub / 4; i += blockDim.x) s_bits[i] = T.ubits[i];
+        if (kBits)
+            for (uint32_t i = threadIdx.x; i < ub / 4; i += blockDim.x) s_bits[i] = T.ubits[i];
+        if (kCmap)
+            for (uint32_t i = threadIdx.x; i < mb / 4; i += blockDim.x) s_cmap[i] = T.cmap[i];
     }
     __syncthreads();
     if constexpr (kPages) V.page = s_page;
@@ -411,6 +424,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     }
     if constexpr (kCompact) V.crange = s_cr;
     if constexpr (kBits) V.ubits = s_bits;
+    if constexpr (kCmap) V.cmap = s_cmap;
     return V;
 }
 

@@ -129,13 +129,23 @@ __device__ __forceinline__ IrrGroup irregular_load(const TView &V, const agile_d
     return G;
 }
 
-// Second half: the four element accesses and gather's output store. Per lane.
-template <int KIND, bool GUARD, int POLICY>
+// How the four element accesses of a lane read the all-user bitmap: each lane its own
+// word (FAST_BITMAP), or once per group of lanes whose elements share a bitmap block, found
+// with __match_any_sync, the group's leader reading the word and __shfl_sync handing it
+// to the others (FAST_MATCH). Both decide the same accesses; the second is kept as a
+// measured alternative.
+enum : int { FAST_BITMAP = 0, FAST_MATCH = 1 };
+
+// Second half: the four element accesses and gather's output store. Per lane; with
+// FAST_MATCH called by all 32 lanes of the warp together.
+template <int KIND, bool GUARD, int POLICY, int FAST = FAST_BITMAP>
 __device__ __forceinline__ void irregular_apply(const TView &V, const agile_dev_table_t &T,
                                                 const IrrGroup &G, float *base, float *out,
                                                 LaneLog &ll) {
     constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
     constexpr bool kGather = KIND == AGILE_IRR_GATHER;
+    unsigned am = kFull;                  // lanes with a group (FAST_MATCH)
+    if constexpr (GUARD && FAST == FAST_MATCH) am = __ballot_sync(kFull, G.act);
     if (!G.act) return;
     float4 *out4 = reinterpret_cast<float4 *>(out);
     float *addr[4];
@@ -150,8 +160,23 @@ __device__ __forceinline__ void irregular_apply(const TView &V, const agile_dev_
         // overlap; an element in an all-user block is then decided without a branch, the
         // rest (blocks that are not all user, denials) by the full classification.
         uint32_t pe[4];
+        if constexpr (FAST == FAST_MATCH) {
+            const uint32_t lane = threadIdx.x & 31;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) pe[k] = user_bits(V, (uint64_t)addr[k]);
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t k0 = ((uint64_t)addr[k] - V.lo) >> V.ulg;
+                const uint32_t blk = k0 < V.un ? (uint32_t)k0 : V.un;
+                const unsigned peers = __match_any_sync(am, blk);
+                const int leader = __ffs(peers) - 1;
+                uint32_t w = 0;
+                if ((int)lane == leader) w = V.ubits[blk >> 5];
+                w = __shfl_sync(am, w, leader);
+                pe[k] = w >> (blk & 31);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pe[k] = user_bits(V, (uint64_t)addr[k]);
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) ok[k] = block_user_fast(V, (uint64_t)addr[k], 4, pe[k]);
 #pragma unroll
@@ -174,13 +199,14 @@ __device__ __forceinline__ void irregular_apply(const TView &V, const agile_dev_
     }
 }
 
-// One group: load, then apply. Warp-collective only in its uniform span checks.
-template <int KIND, bool GUARD, int POLICY>
+// One group: load, then apply. Warp-collective in its uniform span checks (and, with
+// FAST_MATCH, in the bitmap reads).
+template <int KIND, bool GUARD, int POLICY, int FAST = FAST_BITMAP>
 __device__ __forceinline__ void irregular_group(const TView &V, const agile_dev_table_t &T,
                                                 const int64_t *idx, float *base, float *out,
                                                 size_t u0, size_t n4, LaneLog &ll, bool spans) {
     const IrrGroup G = irregular_load<KIND, GUARD, POLICY>(V, T, idx, out, u0, n4, ll, spans);
-    irregular_apply<KIND, GUARD, POLICY>(V, T, G, base, out, ll);
+    irregular_apply<KIND, GUARD, POLICY, FAST>(V, T, G, base, out, ll);
 }
 
 // The n mod 4 tail elements, lanes 0..2 of one warp.

@@ -55,7 +55,7 @@ int agile_module_bind(agile_module_t *m, const agile_dev_table_t *tbl, void *d_l
     AGILE_CUDA_TRY(cudaLibraryGetGlobal(&g_log, &b2, m->lib, "__agile_guard_log"));
     if (b1 != 8 || b2 != 8) return AGILE_ERR_PTX_UNSUPPORTED;
     // The header sits at the start of the table's device buffer.
-    uint64_t vals[2] = {tbl ? (uint64_t)(uintptr_t)tbl->page - 256 : 0, (uint64_t)(uintptr_t)d_log};
+    uint64_t vals[2] = {tbl ? (uint64_t)(uintptr_t)agile::table_buffer(*tbl) : 0, (uint64_t)(uintptr_t)d_log};
     cudaStream_t st = (cudaStream_t)stream;
     AGILE_CUDA_TRY(cudaMemcpyAsync(g_tbl, &vals[0], 8, cudaMemcpyHostToDevice, st));
     AGILE_CUDA_TRY(cudaMemcpyAsync(g_log, &vals[1], 8, cudaMemcpyHostToDevice, st));

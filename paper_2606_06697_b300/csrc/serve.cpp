@@ -8,9 +8,13 @@
 // batching). Requests that carry the same exclusive key never run at the same time, so
 // a request's outputs are the same alone and in the mix.
 //
-// Per launch slot: one stream, one event, one pinned host staging image and one region
-// of the caller's device buffer holding the work list. The worker clock is
-// steady_clock nanoseconds since agile_worker_start.
+// Per launch slot: one stream, one event, one pinned host staging image, one region of the
+// caller's device buffer holding the work list and the per-request done counters, and one
+// host-mapped array of per-request completion notices. A request completes when its
+// notice is raised -- its kernel's last tile is done -- not when its whole launch ends, so
+// a small request packed with a large one does not wait for it; the slot itself is reused
+// only once its launch's event has completed. The worker clock is steady_clock
+// nanoseconds since agile_worker_start.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,16 +34,24 @@
 
 namespace {
 
-size_t slot_bytes(uint32_t max_batch) { return agile_batch_device_bytes(max_batch); }
+// A slot's device region: the batch work list (agile_batch_device_bytes), then one u32
+// done counter per request.
+size_t counters_offset(uint32_t max_batch) { return agile_batch_device_bytes(max_batch); }
+size_t slot_bytes(uint32_t max_batch) {
+    return (counters_offset(max_batch) + 4 * (size_t)max_batch + 255) & ~size_t(255);
+}
 
 struct Slot {
     bool busy = false;
     std::vector<uint32_t> reqs;
-    uint64_t mem = 0;
+    std::vector<char> fin;              // per request of the launch: completed already
+    uint32_t open = 0;                  // requests of the launch not yet completed
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     unsigned char *staging = nullptr;   // pinned
     unsigned char *dev = nullptr;
+    unsigned int *notice = nullptr;     // pinned, mapped: the host's view
+    unsigned int *notice_dev = nullptr; // the same flags as the device addresses them
 };
 
 }  // namespace
@@ -82,6 +94,7 @@ struct agile_worker {
 
     void finish(uint32_t id, int32_t status, uint32_t bad_arg, uint32_t verdict, uint64_t t) {
         agile_completion_t &c = comp[id];
+        if (c.seen_ns == 0) c.seen_ns = t;
         c.tag = reqs[id].tag;
         c.status = status;
         c.bad_arg = bad_arg;
@@ -127,13 +140,24 @@ struct agile_worker {
                 return;
             }
         }
-        if (r.work.table == nullptr)                 // the table buffer starts 256 B before its page map
-            r.work.table = reinterpret_cast<const unsigned char *>(dtab[r.client]->page) - 256;
+        if (r.work.table == nullptr) r.work.table = agile::table_buffer(*dtab[r.client]);
         if (r.work.log == nullptr) r.work.log = dlog[r.client];
         const int rc = agile::batch_check_item(r.work);
         if (rc != AGILE_OK) { finish(id, rc, 0, 0, t); return; }
         if (r.mem_bytes > cfg.mem_budget) { finish(id, AGILE_ERR_TOO_LARGE, 0, 0, t); return; }
+        comp[id].seen_ns = now();
         waiting.push_back(id);
+    }
+
+    // Request k of slot s is done: release its key and memory, complete it.
+    void complete(Slot &s, uint32_t k, int32_t status, uint64_t t) {
+        const uint32_t id = s.reqs[k];
+        s.fin[k] = 1;
+        --s.open;
+        if (reqs[id].excl) busy_keys.erase(reqs[id].excl);
+        admitted -= reqs[id].mem_bytes;
+        admitted_pub.store(admitted);
+        finish(id, status, 0, 0, t);
     }
 
     bool any_busy() const {
@@ -141,17 +165,25 @@ struct agile_worker {
         return false;
     }
 
+    // Complete every request whose notice is up; free a slot once its launch has ended.
     void reap(uint64_t t) {
         for (Slot &s : slots) {
-            if (!s.busy || cudaEventQuery(s.done) != cudaSuccess) continue;
-            for (uint32_t id : s.reqs) {
-                if (reqs[id].excl) busy_keys.erase(reqs[id].excl);
-                finish(id, AGILE_OK, 0, 0, t);
-            }
-            admitted -= s.mem;
-            admitted_pub.store(admitted);
+            if (!s.busy) continue;
+            if (s.open != 0)
+                for (uint32_t k = 0; k < s.reqs.size(); ++k)
+                    if (!s.fin[k] && reinterpret_cast<volatile unsigned int *>(s.notice)[k] != 0)
+                        complete(s, k, AGILE_OK, t);
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaErrorNotReady) continue;
+            // The launch has ended. A notice that is still down can only mean the launch
+            // failed on the device: those requests complete with the error.
+            for (uint32_t k = 0; k < s.reqs.size(); ++k)
+                if (!s.fin[k]) {
+                    const bool up = reinterpret_cast<volatile unsigned int *>(s.notice)[k] != 0;
+                    complete(s, k, up && q == cudaSuccess ? AGILE_OK : AGILE_ERR_CUDA, now());
+                }
             s.reqs.clear();
-            s.mem = 0;
+            s.fin.clear();
             s.busy = false;
         }
     }
@@ -180,34 +212,55 @@ struct agile_worker {
             std::memcpy(s.staging + 64 + 64 * i, &w, 64);
             pre[i + 1] = pre[i] + (w.n + cfg.tile - 1) / cfg.tile;
         }
-        const uint64_t hdr[8] = {n, pre[n], 0, cfg.tile, 0, 0, 0, 0};
+        // header: items, tiles, claim counter, tile, done counters, notices
+        unsigned char *counters = s.dev + counters_offset(cfg.max_batch);
+        const uint64_t hdr[8] = {n, pre[n], 0, cfg.tile, (uint64_t)(uintptr_t)counters,
+                                 (uint64_t)(uintptr_t)s.notice_dev, 0, 0};
         std::memcpy(s.staging, hdr, 64);
+        const size_t list = 64 + 64 * n + 8 * (n + 1);
+        std::memset(s.staging + counters_offset(cfg.max_batch), 0, 4 * n);
+        std::memset(s.notice, 0, 4 * n);
         agile_batch_config_t bc{cfg.tile, 1, 2, 0};
-        int rc = cudaMemcpyAsync(s.dev, s.staging, 64 + 64 * n + 8 * (n + 1), cudaMemcpyHostToDevice,
-                                 s.stream) == cudaSuccess
+        // the work list and, separately, the zeroed done counters
+        int rc = cudaMemcpyAsync(s.dev, s.staging, list, cudaMemcpyHostToDevice, s.stream) == cudaSuccess &&
+                         cudaMemcpyAsync(counters, s.staging + counters_offset(cfg.max_batch), 4 * n,
+                                         cudaMemcpyHostToDevice, s.stream) == cudaSuccess
                      ? agile_batch_launch(s.dev, n, &bc, s.stream)
                      : AGILE_ERR_CUDA;
-        if (cudaEventRecord(s.done, s.stream) != cudaSuccess && rc == AGILE_OK) rc = AGILE_ERR_CUDA;
+        const bool launched = rc == AGILE_OK;
+        const bool recorded = cudaEventRecord(s.done, s.stream) == cudaSuccess;
         const uint32_t seq = launches++;
+        const uint64_t tq = now();
         for (uint32_t id : batch) {
             comp[id].admit_ns = t;
+            comp[id].queued_ns = tq;
             comp[id].launch = seq;
             if (reqs[id].excl) busy_keys.insert(reqs[id].excl);
         }
-        if (rc != AGILE_OK) {                        // nothing ran: complete them with the error
-            cudaStreamSynchronize(s.stream);
-            for (uint32_t id : batch) {
-                if (reqs[id].excl) busy_keys.erase(reqs[id].excl);
-                finish(id, rc, 0, 0, now());
-            }
-            return;
-        }
-        s.reqs = std::move(batch);
-        s.mem = mem;
-        s.busy = true;
         admitted += mem;
         admitted_pub.store(admitted);
         if (admitted > peak_pub.load()) peak_pub.store(admitted);
+        s.reqs = std::move(batch);
+        s.fin.assign(n, 0);
+        s.open = (uint32_t)n;
+        if (!launched || !recorded) {
+            // Nothing was launched, or the kernel was launched but its end cannot be
+            // observed through the event. Either way wait for the stream, then complete
+            // each request by what happened to it: a raised notice means its kernel ran to
+            // the end (its outputs and log are written), so it completes normally -- a
+            // retry of it would apply non-idempotent work such as histogram increments
+            // twice; the others complete with AGILE_ERR_CUDA.
+            cudaStreamSynchronize(s.stream);
+            const uint64_t tf = now();
+            for (uint32_t k = 0; k < n; ++k) {
+                const bool up = launched && reinterpret_cast<volatile unsigned int *>(s.notice)[k] != 0;
+                complete(s, k, up ? AGILE_OK : AGILE_ERR_CUDA, tf);
+            }
+            s.reqs.clear();
+            s.fin.clear();
+            return;
+        }
+        s.busy = true;
     }
 
     void run() {
@@ -280,6 +333,10 @@ int agile_worker_create(const agile_worker_config_t *cfg, const agile_guard_tabl
         cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.staging), sb);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(reinterpret_cast<void **>(&s.notice), 4 * (size_t)cfg->max_batch,
+                              cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.notice_dev), s.notice, 0);
         if (e != cudaSuccess) {
             agile::set_cuda_error((int)e, "worker slot");
             agile_worker_destroy(w);
@@ -340,6 +397,7 @@ void agile_worker_destroy(agile_worker_t *w) {
         if (s.done) cudaEventDestroy(s.done);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.staging) cudaFreeHost(s.staging);
+        if (s.notice) cudaFreeHost(s.notice);
     }
     delete w;
 }

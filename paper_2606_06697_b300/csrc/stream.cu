@@ -14,18 +14,15 @@ using agile::WarpSlots;
 
 constexpr int kThreads = 512;
 
-// Launch shape, measured on the 2^28-element arrays: the guarded kernels run one block of
+// Launch shapes, measured on the 2^28-element arrays: the guarded kernels run one block of
 // 512 threads per SM, each lane keeping 8 units per array in flight (128 registers); the
-// unguarded twins run two blocks per SM with 4 units per lane, their best shape.
-template <bool GUARD> struct Shape;
-template <> struct Shape<true> { static constexpr int kUnits = 8, kBlocksPerSm = 1; };
-template <> struct Shape<false> { static constexpr int kUnits = 4, kBlocksPerSm = 2; };
-
-template <int OP, bool GUARD, int POLICY>
-__global__ void __launch_bounds__(kThreads, Shape<GUARD>::kBlocksPerSm)
+// unguarded twins run two blocks per SM with 4 units per lane, their best shape. Either
+// kind can be launched at either shape (agile_stream_launch_shape), so that the guard's
+// cost can be read at equal shapes.
+template <int OP, bool GUARD, int POLICY, int U, int BPS>
+__global__ void __launch_bounds__(kThreads, BPS)
 k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restrict__ b,
          const float *__restrict__ c, size_t n, float s, LogDev *log) {
-    constexpr int U = Shape<GUARD>::kUnits;
     constexpr uint32_t kTile = 32 * U;
     __shared__ WarpSlots S;
     TView V{};
@@ -48,39 +45,51 @@ k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restri
     if constexpr (GUARD) agile::slots_flush(log, S);
 }
 
-template <int OP, bool GUARD, int POLICY>
+template <int OP, bool GUARD, int POLICY, int U, int BPS>
 int launch(const agile_dev_table_t &T, float *a, const float *b, const float *c, size_t n,
            float s, LogDev *log, cudaStream_t st) {
-    constexpr uint32_t kTile = 32 * Shape<GUARD>::kUnits;
+    constexpr uint32_t kTile = 32 * U;
     const size_t tiles = ((n >> 2) + kTile - 1) / kTile;
     const size_t want = (tiles * 32 + kThreads - 1) / kThreads;
-    const size_t cap = (size_t)agile::sm_count() * Shape<GUARD>::kBlocksPerSm;
+    const size_t cap = (size_t)agile::sm_count() * BPS;
     const unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
-    k_stream<OP, GUARD, POLICY><<<blocks, kThreads, 0, st>>>(T, a, b, c, n, s, log);
+    k_stream<OP, GUARD, POLICY, U, BPS><<<blocks, kThreads, 0, st>>>(T, a, b, c, n, s, log);
     AGILE_CUDA_TRY(cudaGetLastError());
     return AGILE_OK;
 }
 
+// Shape 0: 8 units x 1 block per SM; shape 1: 4 units x 2 blocks per SM.
+template <int OP, bool GUARD, int POLICY>
+int launch_shape(int shape, const agile_dev_table_t &T, float *a, const float *b, const float *c,
+                 size_t n, float s, LogDev *log, cudaStream_t st) {
+    return shape == 0 ? launch<OP, GUARD, POLICY, 8, 1>(T, a, b, c, n, s, log, st)
+                      : launch<OP, GUARD, POLICY, 4, 2>(T, a, b, c, n, s, log, st);
+}
+
 template <int OP>
 int dispatch(const agile_dev_table_t *tbl, float *a, const float *b, const float *c, size_t n,
-             float s, int policy, LogDev *log, cudaStream_t st) {
+             float s, int policy, LogDev *log, int shape, cudaStream_t st) {
     if (tbl == nullptr) {
         agile_dev_table_t none = {};
-        return launch<OP, false, AGILE_POLICY_REPORT>(none, a, b, c, n, s, nullptr, st);
+        return launch_shape<OP, false, AGILE_POLICY_REPORT>(shape < 0 ? 1 : shape, none, a, b, c, n, s,
+                                                            nullptr, st);
     }
+    if (shape < 0) shape = 0;
     switch (policy) {
-        case AGILE_POLICY_POISON: return launch<OP, true, AGILE_POLICY_POISON>(*tbl, a, b, c, n, s, log, st);
-        case AGILE_POLICY_SINK: return launch<OP, true, AGILE_POLICY_SINK>(*tbl, a, b, c, n, s, log, st);
-        case AGILE_POLICY_REPORT: return launch<OP, true, AGILE_POLICY_REPORT>(*tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_POISON:
+            return launch_shape<OP, true, AGILE_POLICY_POISON>(shape, *tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_SINK:
+            return launch_shape<OP, true, AGILE_POLICY_SINK>(shape, *tbl, a, b, c, n, s, log, st);
+        case AGILE_POLICY_REPORT:
+            return launch_shape<OP, true, AGILE_POLICY_REPORT>(shape, *tbl, a, b, c, n, s, log, st);
         default: return AGILE_ERR_INVALID_ARG;
     }
 }
 
-}  // namespace
-
-extern "C" int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *d_a,
-                                   const float *d_b, const float *d_c, size_t n, float s,
-                                   int policy, void *d_log, void *stream) {
+// Argument checks and dispatch; shape -1 picks each kind's own shape.
+int stream_launch(int op, const agile_dev_table_t *tbl, float *d_a, const float *d_b,
+                  const float *d_c, size_t n, float s, int policy, void *d_log, int shape,
+                  void *stream) {
     if (op < AGILE_OP_COPY || op > AGILE_OP_TRIAD) return AGILE_ERR_INVALID_ARG;
     if (policy < AGILE_POLICY_POISON || policy > AGILE_POLICY_REPORT) return AGILE_ERR_INVALID_ARG;
     if (n == 0) return AGILE_OK;
@@ -93,8 +102,27 @@ extern "C" int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *
     cudaStream_t st = (cudaStream_t)stream;
     const float *c = op == AGILE_OP_TRIAD ? d_c : d_b;
     switch (op) {
-        case AGILE_OP_COPY: return dispatch<AGILE_OP_COPY>(tbl, d_a, d_b, c, n, s, policy, log, st);
-        case AGILE_OP_SCALE: return dispatch<AGILE_OP_SCALE>(tbl, d_a, d_b, c, n, s, policy, log, st);
-        default: return dispatch<AGILE_OP_TRIAD>(tbl, d_a, d_b, c, n, s, policy, log, st);
+        case AGILE_OP_COPY: return dispatch<AGILE_OP_COPY>(tbl, d_a, d_b, c, n, s, policy, log, shape, st);
+        case AGILE_OP_SCALE: return dispatch<AGILE_OP_SCALE>(tbl, d_a, d_b, c, n, s, policy, log, shape, st);
+        default: return dispatch<AGILE_OP_TRIAD>(tbl, d_a, d_b, c, n, s, policy, log, shape, st);
     }
+}
+
+}  // namespace
+
+extern "C" int agile_stream_launch(int op, const agile_dev_table_t *tbl, float *d_a,
+                                   const float *d_b, const float *d_c, size_t n, float s,
+                                   int policy, void *d_log, void *stream) {
+    return stream_launch(op, tbl, d_a, d_b, d_c, n, s, policy, d_log, -1, stream);
+}
+
+extern "C" int agile_stream_launch_shape(int op, const agile_dev_table_t *tbl, float *d_a,
+                                         const float *d_b, const float *d_c, size_t n, float s,
+                                         int policy, void *d_log, int units, int blocks_per_sm,
+                                         void *stream) {
+    int shape;
+    if (units == 8 && blocks_per_sm == 1) shape = 0;
+    else if (units == 4 && blocks_per_sm == 2) shape = 1;
+    else return AGILE_ERR_INVALID_ARG;
+    return stream_launch(op, tbl, d_a, d_b, d_c, n, s, policy, d_log, shape, stream);
 }

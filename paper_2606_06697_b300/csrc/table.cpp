@@ -16,7 +16,7 @@ namespace {
 constexpr uint32_t PG_MIXED = 0, PG_USER = 1, PG_HOLE = 2, PG_DENY = 3;
 constexpr uint32_t kIdxMask = 0x3FFFFFFFu;
 constexpr uint64_t kMaxPages = 1ull << 26;
-constexpr size_t kHeaderBytes = 128, kZeroOff = 128, kSinkOff = 192, kPageOff = 256;
+using agile::kTableHeaderBytes, agile::kTableZeroOff, agile::kTableSinkOff, agile::kTablePageOff;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -61,6 +61,60 @@ void build_pages(agile_guard_table &t) {
     t.search_steps = steps;
 }
 
+// Class of every block of C = 2^cmap_log2 bytes from lo: 1 inside one user range, 3 inside
+// one protected range, 2 touched by no range, 0 otherwise (an MMIO block, a block holding a
+// range boundary, and the always-open entry past the last block). A block that ends at
+// 2^64 stays 0, so an access ending there reaches the full rule, which finds its end
+// unrepresentable.
+void build_cmap(const agile_guard_table &t, uint32_t *map, uint64_t window) {
+    const uint64_t C = 1ull << t.cmap_log2, nb = t.cmap_n;
+    auto set = [&](uint64_t k, uint32_t code) {
+        map[k >> 4] = (map[k >> 4] & ~(3u << (2 * (k & 15)))) | (code << (2 * (k & 15)));
+    };
+    for (uint64_t k = 0; k < nb; ++k) set(k, 2);
+    for (uint32_t i = 0; i < t.n; ++i) {
+        const uint64_t b = t.base[i] - t.lo, e = t.end[i] - t.lo;   // e <= window
+        const uint64_t k0 = b >> t.cmap_log2, k1 = (e - 1) >> t.cmap_log2;
+        const uint64_t f0 = (b & (C - 1)) ? k0 + 1 : k0;              // first full block
+        const uint64_t f1 = e >> t.cmap_log2;                         // past the last full one
+        const uint32_t code = t.kind[i] == AGILE_USER ? 1u : t.kind[i] == AGILE_PROTECTED ? 3u : 0u;
+        for (uint64_t k = f0; k < f1 && k < nb; ++k) set(k, code);
+        if (k0 < f0) set(k0, 0);                                      // partial first block
+        if (k1 >= f1 && k1 < nb) set(k1, 0);                          // partial last block
+    }
+    set(nb, 0);
+    if (window != 0 && t.lo + window == 0 && nb > 0) set(nb - 1, 0);  // window ends at 2^64
+}
+
+// Page size for AGILE_PAGE_AUTO: the largest page, from 2 MiB down to 4 KiB, at which at
+// least 95% of the user bytes lie in pages that are all one user range (the accesses the
+// page map decides alone), keeping the map within 2^24 entries; failing that, the page
+// size with the largest such share.
+uint32_t auto_page(const agile_guard_table &t) {
+    uint64_t user = 0;
+    for (uint32_t i = 0; i < t.n; ++i)
+        if (t.kind[i] == AGILE_USER) user += t.end[i] - t.base[i];
+    if (user == 0) return 21;
+    uint32_t best = 21;
+    double best_share = -1.0;
+    for (uint32_t lg = 21; lg >= 12; --lg) {
+        uint64_t lo, np;
+        window(t, lg, &lo, &np);
+        if (np > (1ull << 24)) break;
+        uint64_t pure = 0;
+        for (uint32_t i = 0; i < t.n; ++i) {
+            if (t.kind[i] != AGILE_USER) continue;
+            const uint64_t first = (t.base[i] >> lg) + ((t.base[i] & ((1ull << lg) - 1)) != 0);
+            const uint64_t past = t.end[i] >> lg;                            // pages ending in it
+            if (past > first) pure += (past - first) << lg;
+        }
+        const double share = (double)pure / (double)user;
+        if (share > best_share) { best_share = share; best = lg; }
+        if (share >= 0.95) return lg;
+    }
+    return best;
+}
+
 }  // namespace
 
 namespace agile {
@@ -95,7 +149,7 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
                             agile_guard_table_t **out) {
     if (out == nullptr || (n > 0 && h_ranges == nullptr)) return AGILE_ERR_INVALID_ARG;
     *out = nullptr;
-    if (log2_page < 12 || log2_page > 40) return AGILE_ERR_INVALID_ARG;
+    if (log2_page != AGILE_PAGE_AUTO && (log2_page < 12 || log2_page > 40)) return AGILE_ERR_INVALID_ARG;
     if (n > AGILE_MAX_RANGES) return AGILE_ERR_TOO_LARGE;
     for (size_t i = 0; i < n; ++i) {
         if (h_ranges[i].kind > AGILE_MMIO) return AGILE_ERR_BAD_KIND;
@@ -120,7 +174,7 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
             t->id[i] = r.id;
             if (i > 0 && t->base[i] < t->end[i - 1]) { delete t; return AGILE_ERR_OVERLAP; }
         }
-        uint32_t lg = log2_page;
+        uint32_t lg = log2_page == AGILE_PAGE_AUTO ? auto_page(*t) : log2_page;
         window(*t, lg, &t->lo, &t->npages);
         while (t->npages > kMaxPages) {
             ++lg;
@@ -128,7 +182,7 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
         }
         t->log2_page = lg;
         build_pages(*t);
-        size_t off = kPageOff + align256((t->npages + 1) * 4);
+        size_t off = kTablePageOff + align256((t->npages + 1) * 4);
         t->off_base = off; off += align256(n * 8);
         t->off_end = off;  off += align256(n * 8);
         t->off_kind = off; off += align256(n * 4);
@@ -151,6 +205,14 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
         t->ubits_n = (uint32_t)((window >> ulg) + ((window & ((1ull << ulg) - 1)) != 0));
         t->off_ubits = off;
         off += align256(((uint64_t)t->ubits_n + 1 + 31) / 32 * 4);
+        // Block class map for the batch check: 2 bits per block of C = 2^cmap_log2 bytes
+        // (at least 256, as small as keeps the map within 2^19 blocks).
+        uint32_t clg = 8;
+        while (clg < 63 && (window >> clg) + ((window & ((1ull << clg) - 1)) != 0) > (1ull << 19)) ++clg;
+        t->cmap_log2 = clg;
+        t->cmap_n = (uint32_t)((window >> clg) + ((window & ((1ull << clg) - 1)) != 0));
+        t->off_cmap = off;
+        off += align256(((uint64_t)t->cmap_n + 1 + 15) / 16 * 4);
         t->total = off;
         t->staging.assign(t->total, 0);
         {
@@ -164,7 +226,8 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
                 for (; k < k_end; ++k) ub[k >> 5] |= 1u << (k & 31);
             }
         }
-        std::memcpy(t->staging.data() + kPageOff, t->page.data(), t->page.size() * 4);
+        build_cmap(*t, reinterpret_cast<uint32_t *>(t->staging.data() + t->off_cmap), window);
+        std::memcpy(t->staging.data() + kTablePageOff, t->page.data(), t->page.size() * 4);
         if (n) {
             std::memcpy(t->staging.data() + t->off_base, t->base.data(), n * 8);
             std::memcpy(t->staging.data() + t->off_end, t->end.data(), n * 8);
@@ -222,13 +285,13 @@ int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, 
     h.npages = t->npages;
     h.log2_page = t->log2_page;
     h.n = t->n;
-    h.page = (const uint32_t *)(d + kPageOff);
+    h.page = (const uint32_t *)(d + kTablePageOff);
     h.base = (const uint64_t *)(d + t->off_base);
     h.end = (const uint64_t *)(d + t->off_end);
     h.kind = (const uint32_t *)(d + t->off_kind);
     h.id = (const uint32_t *)(d + t->off_id);
-    h.zero_page = d + kZeroOff;
-    h.sink_page = d + kSinkOff;
+    h.zero_page = d + kTableZeroOff;
+    h.sink_page = d + kTableSinkOff;
     h.bytes = t->total;
     h.search_steps = t->search_steps;
     h.remap_or = t->remap_or;
@@ -236,9 +299,12 @@ int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, 
     h.ubits = (const uint32_t *)(d + t->off_ubits);
     h.ubits_log2 = t->ubits_log2;
     h.ubits_n = t->ubits_n;
-    static_assert(sizeof(agile_dev_table_t) <= kHeaderBytes, "header fits");
+    h.cmap = (const uint32_t *)(d + t->off_cmap);
+    h.cmap_log2 = t->cmap_log2;
+    h.cmap_n = t->cmap_n;
+    static_assert(sizeof(agile_dev_table_t) <= kTableHeaderBytes, "header fits");
     std::memcpy(t->staging.data(), &h, sizeof h);
-    std::memset(t->staging.data() + kZeroOff, 0, 128);
+    std::memset(t->staging.data() + kTableZeroOff, 0, 128);
     AGILE_CUDA_TRY(cudaMemcpyAsync(d_buf, t->staging.data(), t->total, cudaMemcpyHostToDevice,
                                    (cudaStream_t)stream));
     *out = h;

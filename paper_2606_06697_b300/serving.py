@@ -108,6 +108,11 @@ class ServedClients:
         r.arrival_ns = g["arrival_ns"]
         return r
 
+    def kernel_bytes(self, i):
+        """Algorithmic bytes of client i's kernel: copy 8, gather 16, histogram 8 per element."""
+        n = self.layouts[i][5]
+        return n * {"copy": 8, "gather": 16, "hist": 8}[self.specs[i]["op"]]
+
     def output(self, i, slot):
         o = self.off[i] + self.layouts[i][3][f"out{slot}"]
         return self.arena[o:o + self.layouts[i][4][f"out{slot}"]]
@@ -132,15 +137,33 @@ def serve(clients: ServedClients, gen_reqs, continuous=True, max_batch=64, max_i
     return done, peak
 
 
-def latency_stats(gen_reqs, done):
-    """p50 / p99 arrival-to-completion latency of the served requests, throughput, and
-    the rejections."""
+def latency_stats(gen_reqs, done, clients=None):
+    """p50 / p99 arrival-to-completion latency of the served requests, throughput, the
+    rejections, and where the time goes: pickup (arrival to validated by the worker),
+    wait (validated to packed into a launch), launch (the copy and kernel queued) and run
+    (queued to the request's completion notice), each as p50 / p99 in microseconds. With
+    `clients`, the algorithmic bytes the served kernels moved per second."""
     ok = [c for c in done if c.status == 0]
     lat = np.array([(c.done_ns - c.arrival_ns) / 1e3 for c in ok])
     span = (max(c.done_ns for c in done) - min(g["arrival_ns"] for g in gen_reqs)) / 1e9
     rej = [c for c in done if c.status == 1]
-    return {"requests": len(gen_reqs), "served": len(ok), "rejected": len(rej),
-            "p50_us": float(np.percentile(lat, 50)) if len(lat) else None,
-            "p99_us": float(np.percentile(lat, 99)) if len(lat) else None,
-            "throughput_rps": len(done) / span if span > 0 else None,
-            "launches": len({c.launch for c in ok})}
+
+    def pct(x):
+        x = np.asarray(x, dtype=np.float64) / 1e3
+        return [round(float(np.percentile(x, 50)), 1), round(float(np.percentile(x, 99)), 1)] \
+            if len(x) else None
+    out = {"requests": len(gen_reqs), "served": len(ok), "rejected": len(rej),
+           "p50_us": float(np.percentile(lat, 50)) if len(lat) else None,
+           "p99_us": float(np.percentile(lat, 99)) if len(lat) else None,
+           "throughput_rps": len(done) / span if span > 0 else None,
+           "launches": len({c.launch for c in ok}),
+           "breakdown_p50_p99_us": {
+               "pickup": pct([c.seen_ns - c.arrival_ns for c in ok]),
+               "wait": pct([c.admit_ns - c.seen_ns for c in ok]),
+               "launch": pct([c.queued_ns - c.admit_ns for c in ok]),
+               "run": pct([c.done_ns - c.queued_ns for c in ok])}}
+    out["requests_per_launch"] = len(ok) / out["launches"] if out["launches"] else None
+    if clients is not None and span > 0:
+        moved = sum(clients.kernel_bytes(gen_reqs[c.tag]["client"]) for c in ok)
+        out["served_gbs"] = moved / span / 1e9
+    return out

@@ -30,7 +30,7 @@ def put(host, off, arr):
     host[off:off + len(b)] = b
 
 
-def run_case(kind, policy, n, log2_page, **kw):
+def run_case(kind, policy, n, log2_page, fast_path="bitmap", **kw):
     r, span, off, idx, key, bad, host, arena, base = setup(n, **kw)
     put(host, off["idx"], key if kind == "hist" else idx)
     t = r.shifted(base)
@@ -38,8 +38,8 @@ def run_case(kind, policy, n, log2_page, **kw):
     arena.copy_(torch.from_numpy(host))
     log = new_log(client=4)
     target = off["bins"] if kind == "hist" else off["t"]
-    ag.agile_irregular_launch(kind, dev, base + off["idx"], base + target,
-                              base + off["out"], n, policy, log)
+    ag.agile_irregular_launch_fastpath(kind, dev, base + off["idx"], base + target,
+                                       base + off["out"], n, policy, log, fast_path)
     rc, rec = ag.agile_violation_log_read(log)
     got = arena.cpu().numpy()
     va = {"t": base + target, "idx": base + off["idx"], "out": base + off["out"]}
@@ -59,6 +59,21 @@ def test_irregular_parity(kind, policy, log2_page):
 @pytest.mark.parametrize("kind", ["gather", "scatter", "hist"])
 def test_irregular_zipf(kind):
     run_case(kind, "poison", 100_000, 16, dist="zipf", stripes=64)
+
+
+@pytest.mark.parametrize("kind", ["gather", "scatter", "hist"])
+@pytest.mark.parametrize("n", [131, 40_003])
+def test_irregular_match_fast_path(kind, n):
+    """The __match_any_sync form of the per-lane bitmap read decides exactly as the
+    per-lane form: outputs and log equal the oracle's (ragged last group included)."""
+    run_case(kind, "poison", n, 16, fast_path="match", frac_bad=0.05)
+    run_case(kind, "poison", n, 16, fast_path="match", dist="zipf", stripes=64, seed=9)
+
+
+def test_irregular_match_fast_path_arguments():
+    with pytest.raises(ag.AgileError):         # the match form is built for POISON only
+        ag.agile_irregular_launch_fastpath("gather", None, 0x1000, 0x2000, 0x3000, 64, "poison",
+                                           None, "match")
 
 
 @pytest.mark.parametrize("n", [1, 3, 4, 5, 131])

@@ -56,6 +56,8 @@ def test_continuous_batching_equals_one_at_a_time():
     mixed, _ = serve(cs, gen, continuous=True, max_batch=32, max_inflight=4)
     st = latency_stats(gen, mixed)
     assert st["served"] == len(gen) and st["launches"] < len(gen)   # requests shared launches
+    for c in mixed:                      # the completion's times follow the request's path
+        assert c.arrival_ns <= c.seen_ns <= c.admit_ns <= c.queued_ns <= c.done_ns
     got = snapshot(cs)
     logs = [ag.agile_violation_log_read(cs.log(i))[1].count for i in range(len(cs.specs))]
     cs.reset()

@@ -195,6 +195,45 @@ def test_host_array_and_selftest_arguments_checked_before_launch():
                                         1.0, 0, None, 0, None) == 0           # nothing to do
     assert lib.agile_stream_launch_host(2, None, 0x1000, 0x1000, None, None, None, None, 64,
                                         1.0, 0, None, 0, None) == -1          # triad without c
+    # Every chunk's checks are made once, up front: a misaligned array or log, or a bad
+    # policy, is refused before any stream, event or copy exists (on this host, with no
+    # device, any CUDA call would come back as AGILE_ERR_CUDA instead).
+    assert lib.agile_stream_launch_host(2, None, 0x1000, 0x1000, 0x2008, None, None, None, 1 << 20,
+                                        1.0, 0, None, 1 << 16, None) == -12   # c misaligned
+    assert lib.agile_stream_launch_host(0, None, 0x1004, 0x1000, None, None, None, None, 64,
+                                        1.0, 0, None, 0, None) == -12         # a misaligned
+    assert lib.agile_stream_launch_host(0, None, 0x1000, 0x1000, None, None, None, None, 64,
+                                        1.0, 0, 0x3008, 0, None) == -12       # log misaligned
+    assert lib.agile_stream_launch_host(0, None, 0x1000, 0x1000, None, None, None, None, 64,
+                                        1.0, 9, None, 0, None) == -1          # unknown policy
     assert lib.agile_selftest_bounded_waits(0x1000, 0x2000, 0, 0x3000, None) == -1
     assert lib.agile_selftest_bounded_waits(0x1000, 0x2000, 2_000_000, 0x3000, None) == -1
     assert lib.agile_selftest_bounded_waits(0x1008, 0x2000, 100, 0x3000, None) == -12
+
+
+def test_auto_page_size():
+    """AGILE_PAGE_AUTO: the largest page at which 95% of the user bytes lie in pages wholly
+    inside one user range. The stress stripes (60 KiB user + 4 KiB protected) need 4 KiB
+    pages; the 4 MiB + 64 KiB stripes are 95% pure at 256 KiB; Table I's huge apertures at
+    2 MiB; every choice keeps the page map within 2^24 entries."""
+    cases = [(syn.irregular_layout(1 << 20, 1 << 18, 60 << 10, 4 << 10, 1 << 10)[0], 12),
+             (syn.irregular_layout(1 << 20)[0], 18),
+             (syn.table1_apertures(), 21)]
+    for r, want in cases:
+        rr = r.shifted(0x7E0000000000) if int(r.base.max()) < 2**40 else r
+        t = ag.agile_guard_table_build(rr.base, rr.size, rr.kind, rr.ident, 0)
+        lg, npages = t.geometry()
+        assert lg == want and npages <= 1 << 24
+        # and the rule by hand at the choice and one step coarser
+        o = np.argsort(rr.base)
+        base, end = rr.base[o].astype(object), (rr.base[o] + rr.size[o]).astype(object)
+        user = rr.kind[o] == syn.KIND_USER
+
+        def share(g):
+            G = 1 << g
+            pure = sum(max(0, (int(e) // G) - (-(-int(b) // G))) * G
+                       for b, e, u in zip(base, end, user) if u)
+            return pure / sum(int(e) - int(b) for b, e, u in zip(base, end, user) if u)
+        assert share(lg) >= 0.95 or lg == 12
+        if lg < 21:
+            assert share(lg + 1) < 0.95
