@@ -429,8 +429,9 @@ AGILE_API void agile_graph_destroy(agile_graph_t *g);
  * synchronization of cudaMalloc/cudaFree, a plugin given no allocator. The caller still
  * provides every input and output. TOO_LARGE above AGILE_BATCH_STATIC_MAX_ITEMS items;
  * other errors as agile_batch_upload. The first call on a device looks up the array's
- * device address, so make it before any stream capture. All calls share the array:
- * calls that overlap on the GPU race. */
+ * device address, so make it before any stream capture; the address is kept for the
+ * process's life, so no call may follow a cudaDeviceReset of that device. All calls share
+ * the array: calls that overlap on the GPU race. */
 AGILE_API int agile_batch_launch_static(const agile_work_t *h_items, size_t n, uint32_t tile,
                                         const agile_batch_config_t *cfg, void *stream);
 

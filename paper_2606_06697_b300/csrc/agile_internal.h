@@ -46,9 +46,17 @@ inline const unsigned char *table_buffer(const agile_dev_table_t &T) {
 // agile_validate_args and by the serving loop's admission checks.
 uint32_t classify_host(const agile_guard_table &t, uint64_t a, uint64_t w, uint32_t *rid);
 
+// Device bytes of a batch work list of n items: the 64-byte header, the items (64 bytes
+// each) and n + 1 tile prefix sums, rounded up to 256 bytes (agile_batch_device_bytes).
+constexpr size_t batch_device_bytes(size_t n) { return (64 + 64 * n + 8 * (n + 1) + 255) & ~size_t(255); }
+
 // Validation of one batch work item (kind, policy, size, alignment), as the batch upload
 // applies it.
 int batch_check_item(const agile_work_t &w);
+
+// agile_batch_launch for a work list image that was copied to the device, claim counter
+// zeroed, on the same stream just before (the serving worker's launches).
+int batch_launch_fresh(void *d_buf, size_t n_items, const agile_batch_config_t *cfg, void *stream);
 
 // Remember the last CUDA error text for agile_strerror-style diagnostics.
 void set_cuda_error(int err, const char *where);

@@ -180,12 +180,12 @@ int check_item(const agile_work_t &w) {
     return AGILE_OK;
 }
 
-int launch_batch(void *d_buf, const agile_batch_config_t *cfg, cudaStream_t st) {
+int launch_batch(void *d_buf, const agile_batch_config_t *cfg, cudaStream_t st, bool reset = true) {
     BatchHdr *H = static_cast<BatchHdr *>(d_buf);
     unsigned char *base = static_cast<unsigned char *>(d_buf);
     // the item count lives on the device; the prefix follows the largest work list the
     // buffer was sized for, which the kernel finds through the header
-    AGILE_CUDA_TRY(cudaMemsetAsync(&H->counter, 0, sizeof(unsigned long long), st));
+    if (reset) AGILE_CUDA_TRY(cudaMemsetAsync(&H->counter, 0, sizeof(unsigned long long), st));
     const int bps = cfg->blocks_per_sm == 1 ? 1 : 2;
     k_batch<<<agile::sm_count() * bps, kThreads, 0, st>>>(
         H, reinterpret_cast<const agile_work_t *>(base + 64),
@@ -204,13 +204,19 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
 
 namespace agile {
 int batch_check_item(const agile_work_t &w) { return check_item(w); }
+
+// A launch over a work list whose image -- claim counter zeroed -- was just copied to the
+// device on the same stream: no separate reset of the counter.
+int batch_launch_fresh(void *d_buf, size_t n_items, const agile_batch_config_t *cfg, void *stream) {
+    agile_batch_config_t c = *cfg;
+    c.reserved = (uint32_t)n_items;
+    return launch_batch(d_buf, &c, (cudaStream_t)stream, false);
+}
 }  // namespace agile
 
 extern "C" {
 
-size_t agile_batch_device_bytes(size_t max_items) {
-    return (prefix_offset(max_items) + 8 * (max_items + 1) + 255) & ~size_t(255);
-}
+size_t agile_batch_device_bytes(size_t max_items) { return agile::batch_device_bytes(max_items); }
 
 int agile_batch_upload(const agile_work_t *h_items, size_t n, uint32_t tile, void *d_buf,
                        size_t bytes, void *stream) {

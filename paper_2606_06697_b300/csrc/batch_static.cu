@@ -26,7 +26,8 @@
 namespace {
 
 constexpr size_t kItems = AGILE_BATCH_STATIC_MAX_ITEMS;
-constexpr size_t kBytes = (64 + 64 * kItems + 8 * (kItems + 1) + 255) & ~size_t(255);
+constexpr size_t kBytes = agile::batch_device_bytes(kItems);   // what agile_batch_upload needs
+static_assert(kBytes >= 64 + 64 * kItems + 8 * (kItems + 1), "the array holds a full work list");
 
 static __device__ __align__(256) unsigned char g_batch_scratch[kBytes];
 

@@ -34,11 +34,11 @@
 
 namespace {
 
-// A slot's device region: the batch work list (agile_batch_device_bytes), then one u32
-// done counter per request.
-size_t counters_offset(uint32_t max_batch) { return agile_batch_device_bytes(max_batch); }
+// A slot's device region: the batch work list of n requests (header, items, tile prefix
+// sums), directly followed by one u32 done counter per request, so one copy carries both.
+size_t list_bytes(size_t n) { return 64 + 64 * n + 8 * (n + 1); }
 size_t slot_bytes(uint32_t max_batch) {
-    return (counters_offset(max_batch) + 4 * (size_t)max_batch + 255) & ~size_t(255);
+    return (list_bytes(max_batch) + 4 * (size_t)max_batch + 255) & ~size_t(255);
 }
 
 struct Slot {
@@ -212,20 +212,17 @@ struct agile_worker {
             std::memcpy(s.staging + 64 + 64 * i, &w, 64);
             pre[i + 1] = pre[i] + (w.n + cfg.tile - 1) / cfg.tile;
         }
-        // header: items, tiles, claim counter, tile, done counters, notices
-        unsigned char *counters = s.dev + counters_offset(cfg.max_batch);
-        const uint64_t hdr[8] = {n, pre[n], 0, cfg.tile, (uint64_t)(uintptr_t)counters,
+        // header: items, tiles, claim counter (zero), tile, done counters, notices
+        const size_t list = list_bytes(n);
+        const uint64_t hdr[8] = {n, pre[n], 0, cfg.tile, (uint64_t)(uintptr_t)(s.dev + list),
                                  (uint64_t)(uintptr_t)s.notice_dev, 0, 0};
         std::memcpy(s.staging, hdr, 64);
-        const size_t list = 64 + 64 * n + 8 * (n + 1);
-        std::memset(s.staging + counters_offset(cfg.max_batch), 0, 4 * n);
+        std::memset(s.staging + list, 0, 4 * n);
         std::memset(s.notice, 0, 4 * n);
         agile_batch_config_t bc{cfg.tile, 1, 2, 0};
-        // the work list and, separately, the zeroed done counters
-        int rc = cudaMemcpyAsync(s.dev, s.staging, list, cudaMemcpyHostToDevice, s.stream) == cudaSuccess &&
-                         cudaMemcpyAsync(counters, s.staging + counters_offset(cfg.max_batch), 4 * n,
-                                         cudaMemcpyHostToDevice, s.stream) == cudaSuccess
-                     ? agile_batch_launch(s.dev, n, &bc, s.stream)
+        // one copy: the work list with its zeroed claim counter, and the zeroed done counters
+        int rc = cudaMemcpyAsync(s.dev, s.staging, list + 4 * n, cudaMemcpyHostToDevice, s.stream) == cudaSuccess
+                     ? agile::batch_launch_fresh(s.dev, n, &bc, s.stream)
                      : AGILE_ERR_CUDA;
         const bool launched = rc == AGILE_OK;
         const bool recorded = cudaEventRecord(s.done, s.stream) == cudaSuccess;
@@ -285,10 +282,13 @@ struct agile_worker {
             if (any_busy()) {
                 std::this_thread::yield();
             } else if (!arrivals.empty()) {
+                // Sleep only through long gaps, waking 1 ms early: a sleep can overrun by
+                // tens of microseconds, which would land on the request's latency. The
+                // last stretch is spent polling.
                 const uint64_t next = arrivals.top().first;
                 const uint64_t t2 = now();
-                if (next > t2 + 20000) std::this_thread::sleep_for(std::chrono::nanoseconds(
-                                           std::min<uint64_t>(next - t2 - 10000, 200000)));
+                if (next > t2 + 1500000) std::this_thread::sleep_for(std::chrono::nanoseconds(next - t2 - 1000000));
+                else std::this_thread::yield();
             } else {
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
             }

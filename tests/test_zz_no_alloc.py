@@ -54,6 +54,37 @@ def test_static_launch_equals_buffer_launch_twice():
         assert snapshot(cs) == want
 
 
+def test_static_launch_full_array_on_a_stream():
+    """AGILE_BATCH_STATIC_MAX_ITEMS items -- the work list and prefix sums fill the fixed
+    array -- on a non-default stream, twice: equal to the buffer launch of the same list.
+    The list repeats a few clients' work; histogram items then count several times, the
+    same number of times on both paths."""
+    specs = syn.client_specs(16, seed=syn.SEED_BASE + 51, median=16 * 1024, lo=4 * 1024,
+                             hi=64 * 1024, table_lo=8, table_hi=64)
+    cs = ClientSet(specs, DEV, log2_pages=(16,), frac_bad=0.01)
+    base = cs.work(0)
+    m = ag.BATCH_STATIC_MAX_ITEMS
+    items = [base[k % len(base)] for k in range(m)]
+    st = torch.cuda.Stream(device=DEV)
+    cs.reset()
+    buf = torch.empty(ag.agile_batch_device_bytes(m), dtype=torch.uint8, device=DEV)
+    torch.cuda.synchronize()                       # the resets (default stream) come first
+    ag.agile_batch_upload(items, 4096, buf, st)
+    ag.agile_batch_launch(buf, m, 4096, stream=st)
+    st.synchronize()
+    want = snapshot(cs)
+    arr = (ag.Work * m)(*items)
+    cfg = ag.abi.BatchConfig(4096, 1, 2, 0)
+    for _ in range(2):
+        cs.reset()
+        torch.cuda.synchronize()
+        rc = ag.lib().agile_batch_launch_static(arr, m, 4096, ctypes.byref(cfg),
+                                                ctypes.c_void_p(st.cuda_stream))
+        assert rc == 0
+        st.synchronize()
+        assert snapshot(cs) == want
+
+
 def test_static_launch_rejects_too_many_items():
     items = [ag.Work() for _ in range(ag.BATCH_STATIC_MAX_ITEMS + 1)]
     with pytest.raises(ag.AgileError) as e:
