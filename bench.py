@@ -398,7 +398,7 @@ def run_ours(args, ws, rank, local):
     irregular = irregular_sweep(ag, torch, dev, stream, n=args.irregular_n,
                                 stripes=args.irregular_stripes, kinds=args.irregular_kinds.split(","),
                                 dists=args.irregular_dists.split(","),
-                                stress="gather" in args.irregular_kinds) \
+                                stress="gather" in args.irregular_kinds and args.irregular_stress) \
         if "irregular" in args.legs else None
     clients = batch_clients(ag, torch, dev, stream) if "clients" in args.legs else None
     serving = serve_sweep(ag, torch, dev) if "serving" in args.legs else None
@@ -470,6 +470,9 @@ def targets_summary(guarded, unguarded_best, by_shape, ptx_gbs, ptx_plain_gbs, p
             k: _r(v["guarded_over_unguarded"]) for k, v in irregular.items()}
         t["irregular_ptx_table_over_plain"] = {
             k: _r(v["ptx_table_over_plain"]) for k, v in irregular.items() if "ptx_table_over_plain" in v}
+        t["irregular_ptx_table_over_plain_2_blocks_per_sm"] = {
+            k: _r(v["ptx_table_over_plain_two_blocks_per_sm"]) for k, v in irregular.items()
+            if "ptx_table_over_plain_two_blocks_per_sm" in v}
     if clients:
         t["clients_graph_speedup"] = _r(clients["speedup_graph_vs_separate"], 2)
     if serving:
@@ -741,6 +744,29 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096,
                 ms = statistics.median(ts)
                 row[label] = {"ms": ms, "useful_gbs": useful[kind] * n / ms / 1e6}
             row["ptx_table_over_plain"] = row["ptx_plain"]["ms"] / row["ptx_table_64KiB"]["ms"]
+            # the same two modules launched with half the blocks (two 512-thread blocks per
+            # SM): as many as the instrumented kernel keeps resident at its register count
+            half = {}
+            for label in ("ptx_table_64KiB", "ptx_plain"):
+                mod = ptx_mods[label]
+                if label != "ptx_plain":
+                    ag.agile_module_bind(mod, tabs[16][2], log)
+                if kind == "hist":
+                    bins_t.zero_()
+                ag.agile_module_launch(mod, f"agile_ptx_{kind}", grid // 2, 512, args_, stream)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ag.agile_module_launch(mod, f"agile_ptx_{kind}", grid // 2, 512, args_, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                half[label] = statistics.median(ts)
+            row["ptx_two_blocks_per_sm_ms"] = half
+            row["ptx_table_over_plain_two_blocks_per_sm"] = half["ptx_plain"] / half["ptx_table_64KiB"]
             res[f"{kind}_{dist}"] = row
         del element, key
     for mod in ptx_mods.values():
@@ -815,7 +841,7 @@ def irregular_stress(ag, torch, dev, stream, n, reps, stripes=1 << 18):
     return row
 
 
-def serve_sweep(ag, torch, dev, rates=(1e3, 3e3, 1e4, 3e4, 1e5), window_s=0.3, min_requests=3000):
+def serve_sweep(ag, torch, dev, rates=(1e3, 3e3, 1e4, 3e4, 1e5), window_s=0.3, min_requests=6000):
     """64 clients' validate + guarded-launch requests with Poisson arrivals; 0.5% carry a
     bad pointer. Continuous batching against one request at a time, per arrival rate:
     p50/p99 arrival-to-completion latency, its breakdown, and throughput; at the top rate
@@ -926,6 +952,8 @@ def main():
     ap.add_argument("--irregular-stripes", type=int, default=4096)
     ap.add_argument("--irregular-kinds", default="gather,scatter,hist")
     ap.add_argument("--irregular-dists", default="uniform,zipf")
+    ap.add_argument("--irregular-stress", type=int, default=1,
+                    help="0: leave out the 16 GiB stress layout (small profiling runs)")
     args = ap.parse_args()
     args.legs = {"unguarded", "ptx", "batch", "irregular", "clients", "serving", "e2e", "cpu"} \
         if args.legs == "all" else set(args.legs.split(","))
