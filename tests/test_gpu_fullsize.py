@@ -23,6 +23,15 @@ def _irregular_full(dist):
     return n, r, off, idx, key, bad, arena, base
 
 
+def _first_fault(rec, table, a, site=2):
+    """Every field of the log's first record against the oracle's verdict for the access
+    with the smallest address among the denied ones (4-byte element accesses)."""
+    ov, orid, _ = oracle.check_batch(table, np.array([a], np.uint64), np.array([4], np.uint8),
+                                     method="sorted")
+    assert (rec.key, rec.addr, rec.width, rec.site, rec.verdict, rec.range_id) == \
+        (a, a, 4, site, int(ov[0]), int(orid[0])), rec
+
+
 def test_irregular_full_size_scatter_and_histogram():
     """Scatter: the guarded result equals an unguarded scatter of the allowed indices alone
     over the whole 16 GiB table region, protected tails included. Histogram: the guarded
@@ -42,7 +51,7 @@ def test_irregular_full_size_scatter_and_histogram():
     rc, rec = ag.agile_violation_log_read(log)
     nb = int(bad.sum())
     assert rc == 1 and rec.count == nb and rec.site == 2 and rec.verdict == 1
-    assert rec.key == base + 4 * int(idx[bad].min())
+    _first_fault(rec, r.shifted(base), base + 4 * int(idx[bad].min()))
     guarded = tview.clone()
     tview.copy_(init)
     good = d_idx[~d_bad].contiguous()
@@ -57,6 +66,7 @@ def test_irregular_full_size_scatter_and_histogram():
     ag.agile_irregular_launch("hist", dev, d_idx, base + off["bins"], None, n, "poison", log)
     rc, rec = ag.agile_violation_log_read(log)
     assert rc == 1 and rec.count == nb
+    _first_fault(rec, r.shifted(base), base + off["bins"] + 4 * int(key[bad].min()))
     want = torch.bincount(d_idx[~d_bad], minlength=1 << 20).to(torch.int32)
     assert torch.equal(bins[:1 << 20], want) and int(bins[1 << 20:].abs().sum()) == 0
 
@@ -79,6 +89,7 @@ def test_irregular_full_size_gather_zipf():
     d_bad = torch.from_numpy(bad).to(DEV)
     assert torch.equal(g[~d_bad], out[~d_bad]) and bool((g[d_bad] == 0).all())
     assert rc == 1 and rec.count == int(bad.sum())
+    _first_fault(rec, r.shifted(base), base + 4 * int(idx[bad].min()))
     sample = syn.Stream(19, 19).below(n, 2048)
     s_idx = torch.from_numpy(idx[sample]).to(DEV)
     assert torch.equal(g[torch.from_numpy(sample).to(DEV)],
