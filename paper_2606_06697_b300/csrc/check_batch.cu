@@ -262,134 +262,6 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     agile::block_log_flush(log, ll);
 }
 
-// Entries of a warp's queue of open accesses: {address, index | width << 56}.
-constexpr uint32_t kQueueCap = 160;     // 31 carried over + 128 from half a group, rounded up
-constexpr uint32_t kQueueBytes = 32 * kQueueCap * 16;   // per block (32 warps)
-
-// Queue form: pass 1 as above; the open accesses go, with their address and width, into
-// a per-warp queue in shared memory, and pass 2 runs whenever 32 are waiting -- every
-// round with all 32 lanes busy, none re-reading its access from global memory.
-template <int MODE, bool C32, int kG>
-__global__ void __launch_bounds__(kThreads, 1)
-k_check_batch_q(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
-                const uint8_t *__restrict__ width, uint8_t *__restrict__ verdict, size_t n,
-                LogDev *log, uint32_t table_smem) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long s_bar;
-    const TView V = agile::stage_table<MODE>(T, smem, &s_bar, log);
-
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t nthreads = (size_t)gridDim.x * blockDim.x;
-    const size_t ngroups = n / 8;
-    const uint32_t lane = threadIdx.x & 31;
-    uint4 *Q = reinterpret_cast<uint4 *>(smem + table_smem) + (threadIdx.x >> 5) * kQueueCap;
-    uint32_t qn = 0;                   // entries waiting (warp-uniform)
-    LaneLog ll;
-    uint32_t cnt1 = 0;
-    size_t first1 = ~(size_t)0;
-
-    auto decide_entry = [&](const uint4 e) {
-        const uint64_t a = (uint64_t)e.y << 32 | e.x;
-        const uint64_t meta = (uint64_t)e.w << 32 | e.z;
-        const size_t i = meta & ((1ull << 56) - 1);
-        const uint32_t w = (uint32_t)(meta >> 56);
-        uint32_t rid;
-        const uint32_t v = full_rule<C32>(V, a, w, &rid);
-        if (v != AGILE_ALLOW) {
-            ll.note(i, agile::pack_info(0, v, w, rid), a);
-            verdict[i] = (uint8_t)v;
-        }
-    };
-
-    for (size_t g0 = (tid - lane) * kG; g0 < ngroups; g0 += nthreads * kG) {   // warp-uniform
-#pragma unroll
-        for (int h = 0; h < kG; ++h) {
-            const size_t g = g0 + 32 * h + lane;
-            const bool valid = g < ngroups;
-            uint64_t av[8];
-            uint64_t wv = 0;
-            uint32_t ob = 0;           // nibble k's low bit: access k is open
-            if (valid) {
-                const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint4 q = __ldcs(pa + k);
-                    av[2 * k] = (uint64_t)q.y << 32 | q.x;
-                    av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
-                }
-                wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
-                uint32_t sel = 0;
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    sel += cmap_code<C32>(V, av[k], (uint32_t)(wv >> (8 * k)) & 0xFFu) << (4 * k);
-                const uint32_t vlo = __byte_perm(0x01040000u, 0u, sel);
-                const uint32_t vhi = __byte_perm(0x01040000u, 0u, sel >> 16);
-                __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8),
-                       (unsigned long long)vhi << 32 | vlo);
-                const uint32_t nz = (sel | (sel >> 1)) & 0x11111111u;
-                ob = ~nz & 0x11111111u;
-                const uint32_t dn = (sel >> 1) & 0x11111111u;
-                cnt1 += __popc(dn);
-                if (dn != 0 && first1 == ~(size_t)0) first1 = g * 8 + ((__ffs(dn) - 1) >> 2);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) av[k] = 0;
-            }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const uint32_t hb = ob & (half ? 0x11110000u : 0x00001111u);
-                const uint32_t c = __popc(hb);
-                uint32_t incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(agile::kFull, incl, o);
-                    if (lane >= (uint32_t)o) incl += t;
-                }
-                uint32_t pos = qn + incl - c;
-#pragma unroll
-                for (int k = 4 * half; k < 4 * half + 4; ++k)
-                    if ((hb >> (4 * k)) & 1u) {
-                        const uint64_t meta = (uint64_t)(g * 8 + k) | (((wv >> (8 * k)) & 0xFFull) << 56);
-                        Q[pos++] = make_uint4((uint32_t)av[k], (uint32_t)(av[k] >> 32), (uint32_t)meta,
-                                              (uint32_t)(meta >> 32));
-                    }
-                qn += __shfl_sync(agile::kFull, incl, 31);
-                __syncwarp();
-                while (qn >= 32) {                     // full rounds only
-                    qn -= 32;
-                    decide_entry(Q[qn + lane]);
-                    __syncwarp();
-                }
-            }
-        }
-    }
-    if (lane < qn) decide_entry(Q[lane]);              // what is left: one partial round
-    if (blockIdx.x == 0 && threadIdx.x < 32) {        // the last n % 8 accesses
-        const size_t i = ngroups * 8 + threadIdx.x;
-        if (i < n) {
-            const uint64_t a = addr[i];
-            const uint32_t w = width[i];
-            uint32_t rid;
-            const uint32_t v = full_rule<C32>(V, a, w, &rid);
-            if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
-            verdict[i] = (uint8_t)v;
-        }
-    }
-    if (first1 != ~(size_t)0) {
-        const uint64_t a = addr[first1];
-        const uint32_t w = width[first1];
-        uint32_t rid;
-        const uint32_t v = full_rule<C32>(V, a, w, &rid);
-        if (ll.cnt == 0 || first1 < ll.key) {
-            ll.key = first1;
-            ll.info = agile::pack_info(0, v, w, rid);
-            ll.addr = a;
-        }
-    }
-    ll.cnt += cnt1;
-    agile::block_log_flush(log, ll);
-}
-
 // Inputs not aligned for vector loads: one access per thread per step, full rule.
 template <int MODE, bool C32>
 __global__ void __launch_bounds__(kThreads, 1)

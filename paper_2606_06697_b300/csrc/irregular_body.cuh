@@ -56,7 +56,12 @@ __device__ __forceinline__ float element(const TView &V, float *addr, bool ok, i
         }
     }
     if constexpr (KIND == AGILE_IRR_GATHER) {
-        return __ldg((ok || kAlways) ? addr : reinterpret_cast<const float *>(T.zero_page));
+        // Read-only load with a 64-byte L2 fetch hint: for uniform random elements it
+        // measured 3% faster than the default (256 B hint: 4% slower; .cg/.ca/.cs: no change)
+        const float *p = (ok || kAlways) ? addr : reinterpret_cast<const float *>(T.zero_page);
+        float v;
+        asm volatile("ld.global.nc.L2::64B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
     } else if constexpr (KIND == AGILE_IRR_SCATTER) {
         const float f = (float)((uint64_t)e & 0xFFFFFFu);
         if (ok || kAlways) *addr = f;

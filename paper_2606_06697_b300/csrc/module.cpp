@@ -59,20 +59,6 @@ int agile_module_bind(agile_module_t *m, const agile_dev_table_t *tbl, void *d_l
     cudaStream_t st = (cudaStream_t)stream;
     AGILE_CUDA_TRY(cudaMemcpyAsync(g_tbl, &vals[0], 8, cudaMemcpyHostToDevice, st));
     AGILE_CUDA_TRY(cudaMemcpyAsync(g_log, &vals[1], 8, cudaMemcpyHostToDevice, st));
-    // The inline fast check's constants (table rule only): window start, bitmap blocks,
-    // bitmap, log2 block size, zero page, sink page, block size - 1, block size.
-    uint64_t fast[8] = {};
-    if (tbl != nullptr && !m->aperture) {
-        const uint64_t B = 1ull << tbl->ubits_log2;
-        fast[0] = tbl->lo; fast[1] = tbl->ubits_n; fast[2] = (uint64_t)(uintptr_t)tbl->ubits;
-        fast[3] = tbl->ubits_log2; fast[4] = (uint64_t)(uintptr_t)tbl->zero_page;
-        fast[5] = (uint64_t)(uintptr_t)tbl->sink_page; fast[6] = B - 1; fast[7] = B;
-        void *g_fast = nullptr;
-        size_t b3 = 0;
-        AGILE_CUDA_TRY(cudaLibraryGetGlobal(&g_fast, &b3, m->lib, "__agile_fast"));
-        if (b3 != sizeof fast) return AGILE_ERR_PTX_UNSUPPORTED;
-        AGILE_CUDA_TRY(cudaMemcpyAsync(g_fast, fast, sizeof fast, cudaMemcpyHostToDevice, st));
-    }
     AGILE_CUDA_TRY(cudaStreamSynchronize(st));
     m->bound = true;
     return AGILE_OK;

@@ -317,42 +317,36 @@ class Rewriter {
     }
 
     std::string prologue() const {
-        // Per slot: the access's address and its fast-check result, computed ahead of the
-        // access (a straight-line run keeps up to kSlots such checks in flight).
-        const std::string slots = "\t.reg .b64 %__agA<" + std::to_string(kSlots) + ">;\n\t.reg .pred %__agF<" +
-                                  std::to_string(kSlots) + ">;\n";
         if (aperture_)
             return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b64 %__agd<8>;\n"
-                   "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n" + slots +
+                   "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
                    "\tmov.u64 %__agT3, __agile_zero_page;\n"
                    "\tmov.u64 %__agT4, __agile_sink_page;\n";
         // The fast test reads the all-user block bitmap: T0 = window start, T1 = blocks
-        // in the window, T2 = bitmap, lg = log2 of the block size, T3/T4 = zero/sink page,
-        // T6 = block size - 1, T5 = block size -- all uniform, from constant memory.
+        // in the window, T2 = bitmap, lg = log2 of the block size, T5 = block size,
+        // T6 = block size - 1 (header offsets 0, 124, 112, 120).
         return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<8>;\n"
-               "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n" + slots +
-               "\tld.const.u64 %__agT0, [__agile_fast];\n"
-               "\tld.const.u64 %__agT1, [__agile_fast+8];\n"
-               "\tld.const.u64 %__agT2, [__agile_fast+16];\n"
-               "\tld.const.u32 %__agTlg, [__agile_fast+24];\n"
-               "\tld.const.u64 %__agT3, [__agile_fast+32];\n"
-               "\tld.const.u64 %__agT4, [__agile_fast+40];\n"
-               "\tld.const.u64 %__agT6, [__agile_fast+48];\n"
-               "\tld.const.u64 %__agT5, [__agile_fast+56];\n";
+               "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
+               "\tld.global.u64 %__agT7, [__agile_guard_table];\n"
+               "\tld.global.u64 %__agT0, [%__agT7];\n"
+               "\tld.global.u32 %__agr0, [%__agT7+124];\n"
+               "\tcvt.u64.u32 %__agT1, %__agr0;\n"
+               "\tld.global.u32 %__agTlg, [%__agT7+120];\n"
+               "\tld.global.u64 %__agT2, [%__agT7+112];\n"
+               "\tld.global.u64 %__agT3, [%__agT7+64];\n"
+               "\tld.global.u64 %__agT4, [%__agT7+72];\n"
+               "\tmov.b64 %__agT5, 1;\n"
+               "\tshl.b64 %__agT5, %__agT5, %__agTlg;\n"
+               "\tsub.s64 %__agT6, %__agT5, 1;\n";
     }
 
     // ---------------------------------------------------------------- statements
 
-    static constexpr int kSlots = 8;       // fast checks in flight ahead of their accesses
-
-    // One statement of a function body, as the scheduler of a straight-line run sees it.
+    // One statement of a function body.
     struct Stmt {
-        enum Kind { BARRIER, PURE, MEM, ACCESS } kind = BARRIER;
+        enum Kind { OTHER, ACCESS } kind = OTHER;
         std::string lead;                  // whitespace, comments and labels before it
-        std::string lead_cl;               // the same, comments blanked
         std::string text;                  // the statement itself, raw, up to and incl. ';'
-        std::string cl;                    // the same, comments blanked
-        std::vector<std::string> reads, writes;
         // ACCESS only
         Access acc;
         std::string opcode, pred, addr_inner;
@@ -361,57 +355,13 @@ class Rewriter {
         int site = 0;
     };
 
-    // Register names (%name, component suffixes dropped) in a piece of clean text.
-    static void regs_in(const std::string &t, std::vector<std::string> &out) {
-        for (size_t k = 0; k < t.size(); ++k) {
-            if (t[k] != '%') continue;
-            size_t e = k + 1;
-            while (e < t.size() && is_ident(t[e])) ++e;
-            if (e > k + 1) out.push_back(t.substr(k, e - k));
-            k = e - 1;
-        }
-    }
-
-    // Operands after the opcode, split at top-level commas.
-    static std::vector<std::string> operands(const std::string &t) {
-        std::vector<std::string> out;
-        int depth = 0;
-        std::string cur;
-        for (char c : t) {
-            if (c == '{' || c == '[') ++depth;
-            if (c == '}' || c == ']') --depth;
-            if (c == ',' && depth == 0) { out.push_back(cur); cur.clear(); continue; }
-            if (c == ';') break;
-            cur += c;
-        }
-        if (!trim(cur).empty()) out.push_back(cur);
-        return out;
-    }
-
-    // Register arithmetic that may move past memory accesses: no side effects, no implicit
-    // state (carry flag), nothing warp-collective.
-    static bool pure_opcode(const std::string &base, const std::vector<std::string> &mods) {
-        static const char *ok[] = {"mov", "add", "sub", "mul", "mad", "mul24", "mad24", "sad", "shl",
-                                   "shr", "and", "or", "xor", "not", "cnot", "lop3", "shf", "bfe",
-                                   "bfi", "prmt", "popc", "clz", "brev", "bfind", "min", "max",
-                                   "abs", "neg", "selp", "setp", "set", "slct", "cvt", "cvta",
-                                   "fma", "copysign", "testp", "isspacep"};
-        bool found = false;
-        for (auto o : ok) if (base == o) found = true;
-        if (!found) return false;
-        for (const std::string &m : mods) if (m == "cc") return false;
-        return true;
-    }
-
     std::string rewrite_body(const std::string &body, bool skipped) {
         const std::string clean = blank_comments(body);
         std::string out;
-        std::vector<Stmt> run;
         size_t i = 0, n = clean.size(), stmt = 0;
         int site = 0;
         bool any = false;
         int operand_braces = 0;             // inside a {..} vector operand
-        auto flush = [&]() { out += schedule(run); run.clear(); };
         while (i < n) {
             char ch = clean[i];
             if (ch == '{' && (operand_braces > 0 || !only_labels(clean.substr(stmt, i - stmt)))) {
@@ -421,31 +371,23 @@ class Rewriter {
                 --operand_braces;
                 ++i;
             } else if (ch == '{' || ch == '}') {
-                flush();
                 out.append(body, stmt, i + 1 - stmt);
                 stmt = ++i;
             } else if (ch == ';') {
                 if (operand_braces != 0) throw Fail{AGILE_ERR_PTX_PARSE};
                 Stmt st = classify(body.substr(stmt, i + 1 - stmt), clean.substr(stmt, i + 1 - stmt),
                                    skipped, site);
-                if (st.kind == Stmt::ACCESS) any = true;
-                if (st.kind == Stmt::BARRIER || skipped) {           // trusted bodies stay as written
-                    flush();
-                    out += st.lead + st.text;
+                if (st.kind == Stmt::ACCESS) {
+                    any = true;
+                    out += st.lead + emit_prep(st) + emit_finish(st);
                 } else {
-                    if (st.lead_cl.find(':') != std::string::npos) {  // a label starts a new run
-                        flush();
-                        out += st.lead;
-                        st.lead.clear();
-                    }
-                    run.push_back(std::move(st));
+                    out += st.lead + st.text;
                 }
                 stmt = ++i;
             } else {
                 ++i;
             }
         }
-        flush();
         if (!trim(clean.substr(stmt)).empty()) throw Fail{AGILE_ERR_PTX_PARSE};
         out.append(body, stmt, n - stmt);
         return any ? prologue() + out : out;
@@ -464,98 +406,6 @@ class Rewriter {
         }
     }
 
-    // Emission order for a straight-line run (no labels inside, no branches, calls or
-    // barriers): every memory access -- guarded or not -- stays in its original order, and
-    // so do the fast checks of the guarded ones; register arithmetic and the fast checks
-    // move up as far as their register dependences allow (read after write, write after
-    // read, write after write). So the fast checks of consecutive accesses (their bitmap
-    // loads) sit together ahead of the first of those accesses instead of one before each.
-    std::string schedule(std::vector<Stmt> &run) {
-        const size_t m = run.size();
-        if (m == 0) return "";
-        bool has_access = false;
-        for (const Stmt &x : run) has_access |= x.kind == Stmt::ACCESS;
-        if (!has_access) {                    // nothing to check: leave the run as written
-            std::string out;
-            for (const Stmt &x : run) out += x.lead + x.text;
-            return out;
-        }
-        // node 2k: statement k (for an access, its finish); node 2k+1: an access's fast check
-        std::vector<std::vector<size_t>> deps(2 * m);
-        for (size_t k = 0; k < m; ++k) {
-            const Stmt &sk = run[k];
-            auto touches = [](const std::vector<std::string> &a, const std::vector<std::string> &b) {
-                for (const std::string &x : a)
-                    for (const std::string &y : b)
-                        if (x == y) return true;
-                return false;
-            };
-            for (size_t j = 0; j < k; ++j) {
-                const Stmt &sj = run[j];
-                const bool mem = sk.kind != Stmt::PURE && sj.kind != Stmt::PURE;
-                if (mem || touches(sj.writes, sk.reads) || touches(sj.reads, sk.writes) ||
-                    touches(sj.writes, sk.writes))
-                    deps[2 * k].push_back(2 * j);
-            }
-            if (sk.kind == Stmt::ACCESS) {
-                std::vector<std::string> ar;
-                regs_in(sk.addr_inner, ar);
-                for (size_t j = 0; j < k; ++j) {
-                    if (touches(run[j].writes, ar)) deps[2 * k + 1].push_back(2 * j);
-                    if (run[j].kind == Stmt::ACCESS) deps[2 * k + 1].push_back(2 * j + 1);   // checks in order
-                }
-                deps[2 * k].push_back(2 * k + 1);
-            }
-        }
-        std::vector<char> done(2 * m, 0);
-        for (size_t k = 0; k < m; ++k)
-            if (run[k].kind != Stmt::ACCESS) done[2 * k + 1] = 1;        // no such node
-        std::vector<int> slot_of(m, -1);
-        std::vector<char> slot_busy(kSlots, 0);
-        auto ready = [&](size_t v) {
-            for (size_t d : deps[v]) if (!done[d]) return false;
-            return true;
-        };
-        std::string out;
-        size_t next_mem = 0;                // next memory statement in original order
-        size_t emitted = 0, total = 0;
-        for (size_t v = 0; v < 2 * m; ++v) total += !done[v];
-        while (emitted < total) {
-            bool progress = true;
-            while (progress) {               // arithmetic and fast checks, as early as allowed
-                progress = false;
-                for (size_t k = 0; k < m; ++k) {
-                    if (run[k].kind == Stmt::PURE && !done[2 * k] && ready(2 * k)) {
-                        out += run[k].lead + run[k].text;
-                        done[2 * k] = 1; ++emitted; progress = true;
-                    }
-                    if (!done[2 * k + 1] && ready(2 * k + 1)) {
-                        int sl = -1;
-                        for (int q = 0; q < kSlots; ++q) if (!slot_busy[q]) { sl = q; break; }
-                        if (sl < 0) break;                            // all slots in flight
-                        slot_busy[sl] = 1;
-                        slot_of[k] = sl;
-                        out += emit_prep(run[k], sl);
-                        done[2 * k + 1] = 1; ++emitted; progress = true;
-                    }
-                }
-            }
-            while (next_mem < m && (run[next_mem].kind == Stmt::PURE || done[2 * next_mem])) ++next_mem;
-            if (next_mem == m) continue;
-            const size_t k = next_mem;
-            if (!ready(2 * k)) throw Fail{AGILE_ERR_PTX_PARSE};          // cannot happen
-            if (run[k].kind == Stmt::ACCESS) {
-                out += run[k].lead + emit_finish(run[k], slot_of[k]);
-                slot_busy[slot_of[k]] = 0;
-            } else {
-                out += run[k].lead + run[k].text;
-            }
-            done[2 * k] = 1;
-            ++emitted;
-        }
-        return out;
-    }
-
     // Parse one statement (raw text up to and including ';') into a Stmt.
     Stmt classify(const std::string &raw, const std::string &cl, bool skipped, int &site) {
         Stmt st;
@@ -569,10 +419,8 @@ class Rewriter {
         }
         const size_t start = k;
         st.lead = raw.substr(0, start);
-        st.lead_cl = cl.substr(0, start);
         st.text = raw.substr(start);
-        st.cl = cl.substr(start);
-        const std::string &c = st.cl;
+        const std::string c = cl.substr(start);
         const size_t cn = c.size();
         size_t q = 0;
         std::string pred;
@@ -589,36 +437,15 @@ class Rewriter {
         const size_t op_start = q;
         while (q < cn && !std::isspace((unsigned char)c[q]) && c[q] != ';') ++q;
         const std::string opcode = c.substr(op_start, q - op_start);
-        if (opcode.empty() || opcode[0] == '.') return st;          // directive: a barrier
+        if (opcode.empty() || opcode[0] == '.') return st;          // directive
         std::vector<std::string> mods = split_dots(opcode);
         const std::string &base = mods[0];
 
         static const char *rejected[] = {"cp", "multimem", "tensormap", "discard", "sust", "suld",
                                          "sured", "cp.async"};
         for (auto r : rejected) if (base == r) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
-        const std::string rest = c.substr(q);
-        std::vector<std::string> ops = operands(rest);
-        const bool memop = base == "ld" || base == "ldu" || base == "st" || base == "atom" || base == "red";
-        // registers read and written (a predicated write may leave the old value: also a read)
-        if (!pred.empty()) st.reads.push_back(pred);
-        const bool has_dest = !memop ? true : (base == "ld" || base == "ldu" || base == "atom");
-        for (size_t o = 0; o < ops.size(); ++o) {
-            if (o == 0 && has_dest) {
-                regs_in(ops[o], st.writes);
-                if (!pred.empty()) regs_in(ops[o], st.reads);
-            } else {
-                regs_in(ops[o], st.reads);
-            }
-        }
-        bool timer = false;
-        for (const std::string &r : st.reads)
-            if (r == "%clock" || r == "%clock64" || r == "%globaltimer" || r == "%globaltimer_lo" ||
-                r == "%globaltimer_hi")
-                timer = true;
-        if (!memop) {
-            st.kind = pure_opcode(base, mods) && !timer ? Stmt::PURE : Stmt::BARRIER;
+        if (base != "ld" && base != "ldu" && base != "st" && base != "atom" && base != "red")
             return st;
-        }
 
         bool global = false, other_space = false;
         int vec = 1, tbytes = 0;
@@ -634,7 +461,7 @@ class Rewriter {
             else if (x == "v8") vec = 8;
             else if (type_bytes(x)) tbytes = type_bytes(x);
         }
-        if (other_space) { ++other_space_; st.kind = Stmt::MEM; return st; }
+        if (other_space) { ++other_space_; return st; }
         if (tbytes == 0) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
 
         size_t lb = c.find('[', q), rb = lb == std::string::npos ? lb : c.find(']', lb);
@@ -656,7 +483,6 @@ class Rewriter {
         }
         if (skipped) {
             ++rep_.skipped;
-            st.kind = Stmt::MEM;
             return st;
         }
         ++rep_.guarded;
@@ -673,12 +499,14 @@ class Rewriter {
         return st;
     }
 
-    // The fast check of an access, into slot sl: its address in %__agA<sl>, and in
-    // %__agF<sl> whether the inline test already allows it. Branch-free.
-    std::string emit_prep(const Stmt &st, int sl) {
-        const std::string A = "%__agA" + std::to_string(sl), F = "%__agF" + std::to_string(sl);
+    // The inline fast check of an access: its address in %__agd0, and in %__agp1 whether
+    // the inline test already allows it. Branch-free.
+    std::string emit_prep(const Stmt &st) {
+        const std::string A = "%__agd0", F = "%__agp1";
         const std::string W = std::to_string(st.acc.width);
-        std::string g = address(st.addr_inner, A);
+        std::string g = "\n\t// agile guard: site " + std::to_string(st.site) + ", " + st.opcode + ", " +
+                        W + " bytes\n";
+        g += address(st.addr_inner, A);
         if (aperture_) {
             // clear of the apertures' hull, and a + w does not wrap
             g += "\tadd.s64 %__agd1, " + A + ", " + W + ";\n"
@@ -708,17 +536,14 @@ class Rewriter {
     }
 
     // The rest of an access's guard -- the slow path when the fast check did not allow it,
-    // then the policy -- and the access itself, its address taken from slot sl.
-    std::string emit_finish(const Stmt &st, int sl) {
+    // then the policy -- and the access itself.
+    std::string emit_finish(const Stmt &st) {
         const Access &acc = st.acc;
         const std::string &pred = st.pred;
         const bool neg = st.neg;
         const std::string W = std::to_string(acc.width);
         const std::string L = "$__AG_OK_" + std::to_string(label_++);
-        std::string g = "\n\t// agile guard: site " + std::to_string(st.site) + ", " + st.opcode + ", " +
-                        W + " bytes\n";
-        g += "\tmov.b64 %__agd0, %__agA" + std::to_string(sl) + ";\n"
-             "\tmov.pred %__agp1, %__agF" + std::to_string(sl) + ";\n";
+        std::string g;
         if (acc.generic)
             g += "\tisspacep.global %__agp2, %__agd0;\n"
                  "\tnot.pred %__agp2, %__agp2;\n"
@@ -773,7 +598,6 @@ class Rewriter {
             g += "\tmov.b64 %__agd5, %__agd0;\n"
                  "\tmov.pred %__agp4, %__agp3;\n"
                  "\t@%__agp3 bra " + R + ";\n"
-                 "\tld.global.u64 %__agT7, [__agile_guard_table];\n"
                  "\tld.global.u64 %__agd6, [%__agT7+104];\n"
                  "\tor.b64 %__agd6, %__agd0, %__agd6;\n"
                  "\t{\n"
