@@ -553,8 +553,9 @@ class Rewriter {
             else g += "\tor.pred %__agp1, %__agp1, " + pred + ";\n";
         }
         g += "\tmov.u32 %__agr2, 1;\n"
-             "\t@%__agp1 bra " + L + ";\n"
-             "\t{\n"
+             "\t@%__agp1 bra " + L + ";\n";
+        if (!aperture_) g += class_map_test(W, L);
+        g += "\t{\n"
              "\t.param .b64 __aga;\n\t.param .b32 __agw;\n\t.param .b32 __ags;\n"
              "\t.param .b32 __agl;\n\t.param .b32 __agret;\n"
              "\tst.param.b64 [__aga], %__agd0;\n"
@@ -630,6 +631,37 @@ class Rewriter {
         }
         g += "\t" + instr;
         return g;
+    }
+
+    // Second inline test, run when the bitmap's block is not all user: the access's block
+    // in the class map (smaller blocks than the bitmap's) is class 1, inside one user
+    // range, and holds the whole access. Its constants come from the table header (class
+    // map 128, log2 block size 136, blocks 140); the block past the window reads class 0.
+    std::string class_map_test(const std::string &W, const std::string &L) const {
+        return "\tld.global.nc.u64 %__agd6, [%__agT7+128];\n"
+               "\tld.global.nc.v2.u32 {%__agr0, %__agr1}, [%__agT7+136];\n"
+               "\tsub.s64 %__agd1, %__agd0, %__agT0;\n"
+               "\tshr.u64 %__agd2, %__agd1, %__agr0;\n"
+               "\tcvt.u64.u32 %__agd3, %__agr1;\n"
+               "\tmin.u64 %__agd2, %__agd2, %__agd3;\n"
+               "\tshr.u64 %__agd3, %__agd2, 4;\n"
+               "\tshl.b64 %__agd3, %__agd3, 2;\n"
+               "\tadd.s64 %__agd3, %__agd3, %__agd6;\n"
+               "\tld.global.nc.u32 %__agr2, [%__agd3];\n"
+               "\tcvt.u32.u64 %__agr1, %__agd2;\n"
+               "\tshl.b32 %__agr1, %__agr1, 1;\n"
+               "\tand.b32 %__agr1, %__agr1, 30;\n"
+               "\tshr.b32 %__agr2, %__agr2, %__agr1;\n"
+               "\tand.b32 %__agr2, %__agr2, 3;\n"
+               "\tmov.b64 %__agd4, 1;\n"
+               "\tshl.b64 %__agd4, %__agd4, %__agr0;\n"
+               "\tsub.s64 %__agd5, %__agd4, 1;\n"
+               "\tand.b64 %__agd5, %__agd1, %__agd5;\n"
+               "\tadd.s64 %__agd5, %__agd5, " + W + ";\n"
+               "\tsetp.le.u64 %__agp2, %__agd5, %__agd4;\n"
+               "\tsetp.eq.and.u32 %__agp2, %__agr2, 1, %__agp2;\n"
+               "\tmov.u32 %__agr2, 1;\n"
+               "\t@%__agp2 bra " + L + ";\n";
     }
 
     // Effective address [base + off] into register `dst`.

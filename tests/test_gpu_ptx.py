@@ -85,6 +85,47 @@ def test_ptx_violations(modules, policy, n):
         assert SITE_MAP[op][rec.site] == olog.site
 
 
+def test_ptx_class_map_tier(modules):
+    """Arrays whose edges sit 256 bytes into 4 KiB bitmap blocks, each between two 256-byte
+    protected ranges: the bitmap's edge blocks are not all user, the class map's 256-byte
+    blocks are, so those accesses are allowed by the second inline test. Outputs equal the
+    plain module's and nothing is logged; one element past b's end is then denied."""
+    n = 3 * 1024 + 64                                  # 12,544 bytes per array
+    nb = 4 * n
+    ob, oc, oa = 4096 + 256, 5 * 4096 + 256, 9 * 4096 + 256
+    ranges = []
+    for k, o in enumerate((ob, oc, oa)):
+        ranges += [(o - 256, 256, 1, 10 + k), (o, nb, 0, 20 + k), (o + nb, 256, 1, 30 + k)]
+    arena = torch.zeros(13 * 4096, dtype=torch.uint8, device=DEV)
+    base = arena.data_ptr()
+    r = syn._ranges([base + x[0] for x in ranges], [x[1] for x in ranges],
+                    [x[2] for x in ranges], [x[3] for x in ranges])
+    t, dev = device_table(r, 12)
+    assert t.geometry()[0] == 12
+    A, B, C = (arena[o:o + nb].view(torch.float32) for o in (oa, ob, oc))
+    b, c = _fill(n, 5)
+    B.copy_(torch.from_numpy(b))
+    C.copy_(torch.from_numpy(c))
+    for op in ("copy", "scale", "triad"):
+        expect = oracle.stream_plain(op, b, c, 3.0)
+        A.fill_(-1.0)
+        log = new_log()
+        ag.agile_module_bind(modules["poison"], dev, log)
+        launch(modules["poison"], op, A, B, C, n)
+        rc, rec = ag.agile_violation_log_read(log)
+        assert rc == 0 and rec.count == 0, op
+        assert (A.cpu().numpy().view(np.uint32) == expect.view(np.uint32)).all(), op
+    # one more element: b's and c's last reads and a's last write land in the protected tails
+    A.fill_(-1.0)
+    log = new_log()
+    ag.agile_module_bind(modules["poison"], dev, log)
+    launch(modules["poison"], "copy", arena[oa:oa + nb + 4].view(torch.float32),
+           arena[ob:ob + nb + 4].view(torch.float32), C, n + 1)
+    rc, rec = ag.agile_violation_log_read(log)
+    assert rc == 1 and rec.count == 2 and rec.verdict == 1
+    assert rec.addr == base + ob + nb and rec.range_id == 30
+
+
 def test_ptx_launch_refused_until_bound():
     m = ag.agile_module_load(ag.agile_guard_instrument_ptx(STREAM, "poison")[0])
     x = torch.zeros(64, dtype=torch.float32, device=DEV)

@@ -49,6 +49,9 @@ def test_stream_kernels_every_access_guarded(policy):
     assert [int(x[2]) for x in s[:8]] == [16, 16, 16, 16, 16, 16, 4, 4]
     calls = 2 * n_acc if policy == "remap" else n_acc     # remap re-checks address | mask
     assert out.count("call (__agret), __agile_guard_check") == calls
+    # the class-map test sits between the bitmap test and the call, once per access
+    assert out.count("ld.global.nc.v2.u32 {%__agr0, %__agr1}, [%__agT7+136];") == n_acc
+    assert out.count("setp.eq.and.u32 %__agp2, %__agr2, 1, %__agp2;") == n_acc
     loads = sum(1 for x in s if x[1].startswith("ld."))
     stores = n_acc - loads
     if policy == "trap":
@@ -99,6 +102,7 @@ def test_aperture_mode_emission():
     assert rep["guarded"] == 28
     assert "__agile_aperture_mode = 1" in out and "__agile_zero_page[64]" in out
     assert "[__agile_guard_table];" not in out.split(".entry", 1)[1]   # no table in the kernels
+    assert "%__agT7+136" not in out                                     # no class-map test
     assert out.count("setp.ge.u64 %__agp1, %__agd0, 0xf8000000000;") == 28      # hull end
     assert out.count("setp.le.u64 %__agp0, %__agd1, 0xf0000000000;") == 28      # hull start
     assert "setp.lt.u64 %q1, %t0, 0xf1000000000;" in out                          # MMIO aperture
