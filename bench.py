@@ -725,6 +725,7 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096,
             for label, mod in ptx_mods.items():
                 if label != "ptx_plain":
                     ag.agile_module_bind(mod, tabs[16][2] if label == "ptx_table_64KiB" else None, log)
+                    ag.agile_violation_log_init(log, 0, stream)
 
                 def once_ptx():
                     ag.agile_module_launch(mod, f"agile_ptx_{kind}", grid, 512, args_, stream)
@@ -743,6 +744,10 @@ def irregular_sweep(ag, torch, dev, stream, n=1 << 28, reps=5, stripes=4096,
                     ts.append(e0.elapsed_time(e1))
                 ms = statistics.median(ts)
                 row[label] = {"ms": ms, "useful_gbs": useful[kind] * n / ms / 1e6}
+                if label == "ptx_table_64KiB":      # every launch logged every denial
+                    rc, rec = ag.agile_violation_log_read(log, stream)
+                    assert rec.count == nb * (reps + 1), ("ptx", kind, dist, rec.count, nb)
+                    row[label]["violations_per_launch"] = rec.count // (reps + 1)
             row["ptx_table_over_plain"] = row["ptx_plain"]["ms"] / row["ptx_table_64KiB"]["ms"]
             # the same two modules launched with half the blocks (two 512-thread blocks per
             # SM): as many as the instrumented kernel keeps resident at its register count

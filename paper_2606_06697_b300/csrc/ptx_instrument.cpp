@@ -138,9 +138,13 @@ class Rewriter {
             injected_ += kApertureGlobalsPtx;
             injected_ += ".global .align 4 .u32 __agile_aperture_mode = 1;\n";
         }
-        injected_ += kGuardCheckHeadPtx;
-        injected_ += aperture_ ? aperture_body() : std::string(kGuardCheckTablePtx);
-        injected_ += kGuardCheckTailPtx;
+        injected_ += kGuardLogPtx;
+        injected_ += kGuardFlushPtx;
+        // The slow path inlined at each access: classification, then the info word in
+        // %t16 (0 when allowed), registers renamed into the pass's own namespace.
+        slow_ = rename_regs((aperture_ ? aperture_body() : std::string(kGuardCheckTablePtx)) +
+                            "$AGC_LOG:\n" + kGuardInfoPtx +
+                            "\tbra.uni $AGC_END;\n$AGC_RET:\n\tmov.b64 %t16, 0;\n$AGC_END:\n");
     }
 
     std::string run(const std::string &ptx) {
@@ -153,6 +157,10 @@ class Rewriter {
             while (k < clean.size() && std::isspace((unsigned char)clean[k])) ++k;
             if (clean.compare(k, 2, "64") != 0) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
         }
+        // Entry functions keep their violations in registers and merge them before they
+        // exit, unless a trap may end the kernel before that (TRAP policy) or a called
+        // function may exit the thread with the entry's registers unmerged.
+        acc_module_ = policy_ != AGILE_POLICY_TRAP && !func_may_exit(clean);
         size_t inject_at = clean.find('\n', as);
         if (inject_at == std::string::npos) inject_at = clean.size();
 
@@ -182,7 +190,7 @@ class Rewriter {
                     std::string name = function_name(header);
                     ++rep_.functions;
                     out += "{";
-                    out += rewrite_body(body, skip_.count(name) != 0);
+                    out += rewrite_body(body, skip_.count(name) != 0, has_token(header, ".entry"));
                     out += "}";
                 } else {
                     out.append(ptx, i, close - i + 1);
@@ -208,6 +216,39 @@ class Rewriter {
 
   private:
     uint32_t other_space_ = 0;
+
+    // True when the body of some .func holds the word "exit" (read as the instruction).
+    static bool func_may_exit(const std::string &clean) {
+        size_t i = 0, n = clean.size(), stmt_start = 0;
+        while (i < n) {
+            const char ch = clean[i];
+            if (ch == ';') {
+                stmt_start = ++i;
+            } else if (ch == '{') {
+                const size_t close = match_brace(clean, i);
+                if (has_token(clean.substr(stmt_start, i - stmt_start), ".func") &&
+                    has_word(clean.substr(i, close - i), "exit"))
+                    return true;
+                i = close + 1;
+                stmt_start = i;
+            } else {
+                ++i;
+            }
+        }
+        return false;
+    }
+
+    // `w` as a whole word: not part of an identifier, a directive, a register or a label.
+    static bool has_word(const std::string &t, const char *w) {
+        const size_t L = std::strlen(w);
+        for (size_t p = t.find(w); p != std::string::npos; p = t.find(w, p + 1)) {
+            const bool left = p == 0 || !(is_ident(t[p - 1]) || t[p - 1] == '.' || t[p - 1] == '%' ||
+                                          t[p - 1] == '$');
+            const bool right = p + L >= t.size() || !is_ident(t[p + L]);
+            if (left && right) return true;
+        }
+        return false;
+    }
 
     // Independent count of ld/ldu/st/atom/red opcode words, by a plain word scan.
     static uint32_t count_access_words(const std::string &clean) {
@@ -236,7 +277,34 @@ class Rewriter {
     bool aperture_;
     uint64_t hull_lo_ = 0, hull_end_ = 0;   // smallest interval holding every aperture
     std::string injected_;
+    std::string slow_;          // the inlined slow path, labels still $AGC_
     int label_ = 0;
+    bool acc_module_ = false;   // entries of this module keep violations in registers
+    bool acc_fn_ = false;       // ... and the function being rewritten is one of them
+
+    // %t<k>, %s<k>, %q<k> of the slow-path template become %__agt<k>, %__ags<k>, %__agq<k>.
+    static std::string rename_regs(const std::string &t) {
+        std::string o;
+        o.reserve(t.size() + t.size() / 4);
+        for (size_t i = 0; i < t.size(); ++i) {
+            o += t[i];
+            if (t[i] == '%' && i + 2 < t.size() && (t[i + 1] == 't' || t[i + 1] == 's' || t[i + 1] == 'q') &&
+                std::isdigit((unsigned char)t[i + 2]))
+                o += "__ag";
+        }
+        return o;
+    }
+
+    // The slow path for the access at `addr` (a 64-bit register) of `width` bytes at
+    // `site`, with labels of its own; leaves the info word in %__agt16, 0 when allowed.
+    std::string inline_check(const std::string &addr, const std::string &width, int site) {
+        const std::string tag = "$__AGC" + std::to_string(label_++) + "_";
+        std::string body = slow_;
+        for (size_t p = body.find("$AGC_"); p != std::string::npos; p = body.find("$AGC_", p + tag.size()))
+            body.replace(p, 5, tag);
+        return "\tmov.b64 %__agt0, " + addr + ";\n\tmov.u32 %__ags0, " + width + ";\n"
+               "\tmov.u32 %__ags1, " + std::to_string(site) + ";\n\tcvt.u64.u32 %__agt1, %__ags0;\n" + body;
+    }
 
     static std::string hex(uint64_t v) {
         char b[24];
@@ -317,15 +385,21 @@ class Rewriter {
     }
 
     std::string prologue() const {
+        // Registers of an accumulating function: count, smallest (key, info).
+        const std::string acc = !acc_fn_ ? std::string()
+            : "\t.reg .b32 %__agc;\n\t.reg .b64 %__agk;\n\t.reg .b64 %__agi;\n"
+              "\tmov.u32 %__agc, 0;\n\tmov.b64 %__agk, 0xFFFFFFFFFFFFFFFF;\n"
+              "\tmov.b64 %__agi, 0xFFFFFFFFFFFFFFFF;\n";
+        const std::string slow = "\t.reg .b64 %__agt<24>;\n\t.reg .b32 %__ags<20>;\n\t.reg .pred %__agq<8>;\n";
         if (aperture_)
-            return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b64 %__agd<8>;\n"
+            return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b64 %__agd<8>;\n" + slow +
                    "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
                    "\tmov.u64 %__agT3, __agile_zero_page;\n"
-                   "\tmov.u64 %__agT4, __agile_sink_page;\n";
+                   "\tmov.u64 %__agT4, __agile_sink_page;\n" + acc;
         // The fast test reads the all-user block bitmap: T0 = window start, T1 = blocks
-        // in the window, T2 = bitmap, lg = log2 of the block size, T5 = block size,
-        // T6 = block size - 1 (header offsets 0, 124, 112, 120).
-        return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<8>;\n"
+        // in the window, T2 = bitmap, lg = log2 of the block size (header offsets 0, 124,
+        // 112, 120); T3, T4 = zero and sink pages, T7 = the table.
+        return "\n\t.reg .b64 %__agT<8>;\n\t.reg .b32 %__agTlg;\n\t.reg .b64 %__agd<8>;\n" + slow +
                "\t.reg .b32 %__agr<3>;\n\t.reg .pred %__agp<5>;\n"
                "\tld.global.u64 %__agT7, [__agile_guard_table];\n"
                "\tld.global.u64 %__agT0, [%__agT7];\n"
@@ -334,20 +408,17 @@ class Rewriter {
                "\tld.global.u32 %__agTlg, [%__agT7+120];\n"
                "\tld.global.u64 %__agT2, [%__agT7+112];\n"
                "\tld.global.u64 %__agT3, [%__agT7+64];\n"
-               "\tld.global.u64 %__agT4, [%__agT7+72];\n"
-               "\tmov.b64 %__agT5, 1;\n"
-               "\tshl.b64 %__agT5, %__agT5, %__agTlg;\n"
-               "\tsub.s64 %__agT6, %__agT5, 1;\n";
+               "\tld.global.u64 %__agT4, [%__agT7+72];\n" + acc;
     }
 
     // ---------------------------------------------------------------- statements
 
     // One statement of a function body.
     struct Stmt {
-        enum Kind { OTHER, ACCESS } kind = OTHER;
+        enum Kind { OTHER, ACCESS, EXIT } kind = OTHER;
         std::string lead;                  // whitespace, comments and labels before it
         std::string text;                  // the statement itself, raw, up to and incl. ';'
-        // ACCESS only
+        // ACCESS (and, for pred and neg, EXIT)
         Access acc;
         std::string opcode, pred, addr_inner;
         bool neg = false;
@@ -355,9 +426,11 @@ class Rewriter {
         int site = 0;
     };
 
-    std::string rewrite_body(const std::string &body, bool skipped) {
+    std::string rewrite_body(const std::string &body, bool skipped, bool entry) {
+        acc_fn_ = entry && acc_module_;
         const std::string clean = blank_comments(body);
         std::string out;
+        std::vector<std::pair<size_t, std::string>> exits;   // flush position, its predicate
         size_t i = 0, n = clean.size(), stmt = 0;
         int site = 0;
         bool any = false;
@@ -381,7 +454,11 @@ class Rewriter {
                     any = true;
                     out += st.lead + emit_prep(st) + emit_finish(st);
                 } else {
-                    out += st.lead + st.text;
+                    out += st.lead;
+                    if (st.kind == Stmt::EXIT)
+                        exits.emplace_back(out.size(), st.pred.empty() ? std::string()
+                                           : "@" + std::string(st.neg ? "!" : "") + st.pred + " ");
+                    out += st.text;
                 }
                 stmt = ++i;
             } else {
@@ -390,7 +467,22 @@ class Rewriter {
         }
         if (!trim(clean.substr(stmt)).empty()) throw Fail{AGILE_ERR_PTX_PARSE};
         out.append(body, stmt, n - stmt);
+        if (any && acc_fn_) {
+            // merge the registers before every ret and exit, and at the end of the body
+            out += flush_call("");
+            for (auto it = exits.rbegin(); it != exits.rend(); ++it)
+                out.insert(it->first, flush_call(it->second));
+        }
         return any ? prologue() + out : out;
+    }
+
+    // Call of __agile_guard_flush with the function's count and smallest record, under
+    // the predicate `pred` of the ret or exit it precedes.
+    static std::string flush_call(const std::string &pred) {
+        return "\n\t{\n\t.param .b32 __agfc;\n\t.param .b64 __agfk;\n\t.param .b64 __agfi;\n"
+               "\tst.param.b32 [__agfc], %__agc;\n\tst.param.b64 [__agfk], %__agk;\n"
+               "\tst.param.b64 [__agfi], %__agi;\n"
+               "\t" + pred + "call __agile_guard_flush, (__agfc, __agfk, __agfi);\n\t}\n";
     }
 
     // True when `t` holds nothing but whitespace and labels: a '{' after it opens a scope.
@@ -441,6 +533,12 @@ class Rewriter {
         std::vector<std::string> mods = split_dots(opcode);
         const std::string &base = mods[0];
 
+        if (base == "ret" || base == "exit") {
+            st.kind = Stmt::EXIT;
+            st.pred = pred;
+            st.neg = neg;
+            return st;
+        }
         static const char *rejected[] = {"cp", "multimem", "tensormap", "discard", "sust", "suld",
                                          "sured", "cp.async"};
         for (auto r : rejected) if (base == r) throw Fail{AGILE_ERR_PTX_UNSUPPORTED};
@@ -516,8 +614,12 @@ class Rewriter {
                  "\tsetp.ge.u64 %__agp0, %__agd1, " + A + ";\n"
                  "\tand.pred " + F + ", " + F + ", %__agp0;\n";
         } else {
+            const std::string W1 = std::to_string(st.acc.width - 1);
             g += "\tsub.s64 %__agd1, " + A + ", %__agT0;\n"                // offset in the window
-                 "\tshr.u64 %__agd2, %__agd1, %__agTlg;\n"                  // block
+                 "\tshr.u64 %__agd2, %__agd1, %__agTlg;\n"                  // block of the first byte
+                 "\tadd.s64 %__agd4, %__agd1, " + W1 + ";\n"
+                 "\tshr.u64 %__agd4, %__agd4, %__agTlg;\n"                  // ... and of the last
+                 "\tsetp.eq.u64 " + F + ", %__agd4, %__agd2;\n"
                  "\tmin.u64 %__agd2, %__agd2, %__agT1;\n"                   // past the window: last bit (clear)
                  "\tshr.u64 %__agd3, %__agd2, 5;\n"
                  "\tshl.b64 %__agd3, %__agd3, 2;\n"
@@ -527,9 +629,6 @@ class Rewriter {
                  "\tand.b32 %__agr1, %__agr1, 31;\n"
                  "\tshr.b32 %__agr0, %__agr0, %__agr1;\n"
                  "\tand.b32 %__agr0, %__agr0, 1;\n"
-                 "\tand.b64 %__agd4, %__agd1, %__agT6;\n"
-                 "\tadd.s64 %__agd4, %__agd4, " + W + ";\n"
-                 "\tsetp.le.u64 " + F + ", %__agd4, %__agT5;\n"
                  "\tsetp.ne.and.u32 " + F + ", %__agr0, 0, " + F + ";\n";
         }
         return g;
@@ -555,16 +654,25 @@ class Rewriter {
         g += "\tmov.u32 %__agr2, 1;\n"
              "\t@%__agp1 bra " + L + ";\n";
         if (!aperture_) g += class_map_test(W, L);
-        g += "\t{\n"
-             "\t.param .b64 __aga;\n\t.param .b32 __agw;\n\t.param .b32 __ags;\n"
-             "\t.param .b32 __agl;\n\t.param .b32 __agret;\n"
-             "\tst.param.b64 [__aga], %__agd0;\n"
-             "\tst.param.b32 [__agw], " + W + ";\n"
-             "\tst.param.b32 [__ags], " + std::to_string(st.site) + ";\n"
-             "\tst.param.b32 [__agl], 1;\n"
-             "\tcall (__agret), __agile_guard_check, (__aga, __agw, __ags, __agl);\n"
-             "\tld.param.b32 %__agr2, [__agret];\n"
-             "\t}\n" + L + ":\n"
+        g += inline_check("%__agd0", W, st.site) +
+             "\tsetp.eq.u64 %__agp2, %__agt16, 0;\n"            // info 0: allowed
+             "\tselp.u32 %__agr2, 1, 0, %__agp2;\n";
+        if (acc_fn_)   // a denial: count + 1, and keep the smaller (address, info)
+            g += "\tsetp.eq.u32 %__agp2, %__agr2, 0;\n"
+                 "\t@%__agp2 add.u32 %__agc, %__agc, 1;\n"
+                 "\tsetp.lt.u64 %__agp0, %__agd0, %__agk;\n"
+                 "\tsetp.eq.u64 %__agp3, %__agd0, %__agk;\n"
+                 "\tsetp.lt.and.u64 %__agp3, %__agt16, %__agi, %__agp3;\n"
+                 "\tor.pred %__agp0, %__agp0, %__agp3;\n"
+                 "\tand.pred %__agp0, %__agp0, %__agp2;\n"
+                 "\t@%__agp0 mov.b64 %__agk, %__agd0;\n"
+                 "\t@%__agp0 mov.b64 %__agi, %__agt16;\n";
+        else           // a denial merged into the log at once
+            g += "\t{\n\t.param .b64 __agmk;\n\t.param .b64 __agmi;\n\t.param .b32 __agmc;\n"
+                 "\tst.param.b64 [__agmk], %__agd0;\n\tst.param.b64 [__agmi], %__agt16;\n"
+                 "\tst.param.b32 [__agmc], 1;\n"
+                 "\t@!%__agp2 call __agile_guard_merge, (__agmk, __agmi, __agmc);\n\t}\n";
+        g += L + ":\n"
              "\tsetp.ne.u32 %__agp3, %__agr2, 0;\n";
 
         // the access itself, address (and for POISON stores the predicate) rewritten
@@ -601,17 +709,8 @@ class Rewriter {
                  "\t@%__agp3 bra " + R + ";\n"
                  "\tld.global.u64 %__agd6, [%__agT7+104];\n"
                  "\tor.b64 %__agd6, %__agd0, %__agd6;\n"
-                 "\t{\n"
-                 "\t.param .b64 __aga;\n\t.param .b32 __agw;\n\t.param .b32 __ags;\n"
-                 "\t.param .b32 __agl;\n\t.param .b32 __agret;\n"
-                 "\tst.param.b64 [__aga], %__agd6;\n"
-                 "\tst.param.b32 [__agw], " + W + ";\n"
-                 "\tst.param.b32 [__ags], 0;\n"
-                 "\tst.param.b32 [__agl], 0;\n"
-                 "\tcall (__agret), __agile_guard_check, (__aga, __agw, __ags, __agl);\n"
-                 "\tld.param.b32 %__agr2, [__agret];\n"
-                 "\t}\n"
-                 "\tsetp.ne.u32 %__agp4, %__agr2, 0;\n"
+                 + inline_check("%__agd6", W, 0) +
+                 "\tsetp.eq.u64 %__agp4, %__agt16, 0;\n"
                  "\tmov.b64 %__agd5, %__agd6;\n" + R + ":\n";
             if (!writes) {
                 g += "\tselp.b64 %__agd5, %__agd5, %__agT3, %__agp4;\n";   // else the zero page

@@ -126,6 +126,77 @@ def test_ptx_class_map_tier(modules):
     assert rec.addr == base + ob + nb and rec.range_id == 30
 
 
+EXITS = """
+.version 9.0
+.target sm_103a
+.address_size 64
+.visible .entry agile_ptx_exits(.param .u64 p_a, .param .u64 p_n)
+{
+    .reg .pred %p<4>;
+    .reg .b32 %r<6>;
+    .reg .b64 %rd<6>;
+    ld.param.u64 %rd1, [p_a];
+    ld.param.u64 %rd2, [p_n];
+    mov.u32 %r1, %tid.x;
+    mov.u32 %r2, %ctaid.x;
+    mov.u32 %r3, %ntid.x;
+    mad.lo.u32 %r4, %r2, %r3, %r1;
+    cvt.u64.u32 %rd3, %r4;
+    setp.ge.u64 %p1, %rd3, %rd2;
+    @%p1 bra $DONE;
+    shl.b64 %rd4, %rd3, 2;
+    add.s64 %rd5, %rd1, %rd4;
+    st.global.u32 [%rd5], %r4;
+    and.b32 %r5, %r4, 3;
+    setp.eq.u32 %p2, %r5, 1;
+    @%p2 ret;
+    setp.eq.u32 %p3, %r5, 2;
+    @%p3 exit;
+    st.global.u32 [%rd5+4], %r4;
+$DONE:
+    ret;
+}
+"""
+
+
+@pytest.mark.parametrize("policy", ["poison", "report"])
+def test_ptx_violations_merged_at_every_exit(policy):
+    """Thread i stores a[i]; threads with i mod 4 = 1 then return and those with
+    i mod 4 = 2 exit; the rest also store a[i + 1]. The array runs past its user range
+    into a protected one, so denials land before each way out. The log -- merged from
+    registers before each ret and exit -- holds the oracle's count and, for the smallest
+    denied address, its record (site 0: the first store)."""
+    n, m = 5000, 3333                                   # threads; elements inside the range
+    arena = torch.zeros(8 << 20, dtype=torch.uint8, device=DEV)
+    base = arena.data_ptr()
+    a = base + 4096
+    r = syn._ranges([a, a + 4 * m], [4 * m, 2 << 20], [0, 1], [7, 8])
+    t, dev = device_table(r, 12)
+    mod = ag.agile_module_load(ag.agile_guard_instrument_ptx(EXITS, policy)[0])
+    try:
+        log = new_log(client=3)
+        ag.agile_module_bind(mod, dev, log)
+        ag.agile_module_launch(mod, "agile_ptx_exits", (n + 255) // 256, 256,
+                               [ctypes.c_uint64(a), ctypes.c_uint64(n)])
+        rc, rec = ag.agile_violation_log_read(log)
+    finally:
+        mod.unload()
+    i = np.arange(n, dtype=np.uint64)
+    second = i[(i % 4 != 1) & (i % 4 != 2)]
+    addrs = np.concatenate([a + 4 * i, a + 4 * (second + 1)]).astype(np.uint64)
+    sites = np.concatenate([np.zeros(n, np.uint32), np.ones(len(second), np.uint32)])
+    v, rid, olog = oracle.check_batch(r, addrs, np.full(len(addrs), 4, np.uint8), method="sorted")
+    denied = v != 0
+    k = np.lexsort((sites[denied], addrs[denied]))[0]   # smallest address, then site
+    assert rc == 1 and rec.count == int(denied.sum()) == olog.count and rec.client == 3
+    assert (rec.addr, rec.site, rec.verdict, rec.range_id, rec.width) == \
+        (int(addrs[denied][k]), int(sites[denied][k]), int(v[denied][k]), int(rid[denied][k]), 4)
+    # every allowed store landed: a[j] holds j, or j - 1 where thread j - 1 stored it second
+    got = arena[4096:4096 + 4 * m].view(torch.int32).cpu().numpy().astype(np.int64)
+    j = np.arange(m)
+    assert ((got == j) | ((got == j - 1) & np.isin((j - 1) % 4, (0, 3)))).all()
+
+
 def test_ptx_launch_refused_until_bound():
     m = ag.agile_module_load(ag.agile_guard_instrument_ptx(STREAM, "poison")[0])
     x = torch.zeros(64, dtype=torch.float32, device=DEV)

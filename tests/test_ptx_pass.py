@@ -17,6 +17,15 @@ STREAM = open(os.path.join(PTX_DIR, "stream.ptx")).read()
 HDR = ".version 9.0\n.target sm_103a\n.address_size 64\n"
 
 
+MERGE_AT_ONCE = "@!%__agp2 call __agile_guard_merge, (__agmk, __agmi, __agmc);"
+KEEP_IN_REGS = "@%__agp2 add.u32 %__agc, %__agc, 1;"
+
+
+def slow_paths(text):
+    """Labels that end each inlined copy of the slow path."""
+    return re.findall(r"\$__AGC\d+_END:", text)
+
+
 def kernel(body, regs=".reg .b64 %rd<8>;\n.reg .f32 %f<8>;\n.reg .b32 %r<8>;\n.reg .pred %p<4>;",
            name="k"):
     return HDR + f".visible .entry {name}(.param .u64 p0)\n{{\n{regs}\nld.param.u64 %rd1, [p0];\n{body}\nret;\n}}\n"
@@ -47,8 +56,17 @@ def test_stream_kernels_every_access_guarded(policy):
     assert [x[1] for x in s[:6]] == ["ld.global.v4.f32", "ld.global.v4.f32", "st.global.v4.f32",
                                      "st.global.v4.f32", "ld.global.v4.f32", "st.global.v4.f32"]
     assert [int(x[2]) for x in s[:8]] == [16, 16, 16, 16, 16, 16, 4, 4]
-    calls = 2 * n_acc if policy == "remap" else n_acc     # remap re-checks address | mask
-    assert out.count("call (__agret), __agile_guard_check") == calls
+    slow = 2 * n_acc if policy == "remap" else n_acc      # remap re-checks address | mask
+    assert len(slow_paths(out)) == slow                      # the slow path, inlined
+    assert "__agile_guard_check" not in out
+    # entry functions keep violations in registers and merge them before each ret; under
+    # TRAP every violation is merged at once, as a trap ends the kernel
+    merged_at_once = policy == "trap"
+    assert out.count(MERGE_AT_ONCE) == (n_acc if merged_at_once else 0)
+    assert out.count(KEEP_IN_REGS) == (0 if merged_at_once else n_acc)
+    rets = len(re.findall(r"\bret;", STREAM))
+    flushes = out.count("call __agile_guard_flush, (__agfc, __agfk, __agfi);")
+    assert flushes == (0 if merged_at_once else rets + 3)     # each ret, and each body's end
     # the class-map test sits between the bitmap test and the call, once per access
     assert out.count("ld.global.nc.v2.u32 {%__agr0, %__agr1}, [%__agT7+136];") == n_acc
     assert out.count("setp.eq.and.u32 %__agp2, %__agr2, 1, %__agp2;") == n_acc
@@ -75,7 +93,7 @@ def test_remap_policy_emission():
     n = rep["guarded"]
     assert n == 28
     assert out.count("ld.global.u64 %__agd6, [%__agT7+104];") == n
-    assert out.count("st.param.b32 [__agl], 0;") == n and out.count("st.param.b32 [__agl], 1;") == n
+    assert len(slow_paths(out)) == 2 * n and out.count(KEEP_IN_REGS) == n
     loads = len(re.findall(r"\bld\.global\.", STREAM))
     assert out.count("selp.b64 %__agd5, %__agd5, %__agT3, %__agp4") == loads
     assert out.count("@%__agp4 st.global") == n - loads
@@ -105,8 +123,9 @@ def test_aperture_mode_emission():
     assert "%__agT7+136" not in out                                     # no class-map test
     assert out.count("setp.ge.u64 %__agp1, %__agd0, 0xf8000000000;") == 28      # hull end
     assert out.count("setp.le.u64 %__agp0, %__agd1, 0xf0000000000;") == 28      # hull start
-    assert "setp.lt.u64 %q1, %t0, 0xf1000000000;" in out                          # MMIO aperture
-    assert "selp.u32 %s2, 2, %s2, %q1;" in out and "selp.u32 %s2, 1, %s2, %q1;" in out
+    assert out.count("setp.lt.u64 %__agq1, %__agt0, 0xf1000000000;") == 28       # MMIO aperture
+    assert out.count("selp.u32 %__ags2, 2, %__ags2, %__agq1;") == 28
+    assert out.count("selp.u32 %__ags2, 1, %__ags2, %__agq1;") == 28
     assemble(out)
     for policy in ("sink", "report", "trap"):
         assemble(ag.agile_guard_instrument_ptx(STREAM, policy, apertures=aps)[0])
@@ -140,6 +159,56 @@ def test_skip_list_leaves_trusted_functions_alone():
     assert rep["guarded"] == 20 and rep["skipped"] == 8 and rep["functions"] == 3
     body = out[out.index(".entry agile_ptx_copy"):out.index(".entry agile_ptx_scale")]
     assert "agile guard" not in body and "__agT" not in body
+    assemble(out)
+
+
+def test_violations_merged_in_registers_only_where_every_exit_is_seen():
+    """Entry functions keep their count and smallest record in registers and merge them
+    before each ret and exit (predicated like it) and at the body's end. A .func keeps
+    merging each violation at once. When some .func can exit the thread, or under TRAP,
+    no function keeps registers."""
+    body = """
+    ld.global.f32 %f1, [%rd1];
+    setp.eq.f32 %p1, %f1, 0f00000000;
+    @%p1 ret;
+    @!%p1 exit;
+    """
+    out, _ = ag.agile_guard_instrument_ptx(kernel(body), "poison")
+    assert out.count(KEEP_IN_REGS) == 1 and MERGE_AT_ONCE not in out
+    assert "@%p1 call __agile_guard_flush" in out and "@!%p1 call __agile_guard_flush" in out
+    assert out.count("call __agile_guard_flush, (__agfc, __agfk, __agfi);") == 4
+    assert out.index("@%p1 call __agile_guard_flush") < out.index("@%p1 ret;")
+    assemble(out)
+    helper = HDR + """
+.func helper(.param .b64 q)
+{
+    .reg .b64 %rd<2>;
+    .reg .f32 %f<2>;
+    ld.param.b64 %rd1, [q];
+    ld.global.f32 %f1, [%rd1];
+    ret;
+}
+.visible .entry k(.param .u64 p0)
+{
+    .reg .b64 %rd<2>;
+    .reg .f32 %f<2>;
+    ld.param.u64 %rd1, [p0];
+    st.global.f32 [%rd1], %f1;
+    ret;
+}
+"""
+    out, rep = ag.agile_guard_instrument_ptx(helper, "poison")
+    assert rep["guarded"] == 2
+    assert out.count(MERGE_AT_ONCE) == 1 and out.count(KEEP_IN_REGS) == 1
+    assemble(out)
+    exiting = helper.replace("    ld.global.f32 %f1, [%rd1];\n    ret;", "    ld.global.f32 %f1, [%rd1];\n    exit;")
+    assert exiting != helper
+    out, _ = ag.agile_guard_instrument_ptx(exiting, "poison")
+    assert out.count(MERGE_AT_ONCE) == 2 and KEEP_IN_REGS not in out
+    assert "call __agile_guard_flush" not in out
+    assemble(out)
+    out, _ = ag.agile_guard_instrument_ptx(kernel(body), "trap")
+    assert KEEP_IN_REGS not in out and "call __agile_guard_flush" not in out
     assemble(out)
 
 
