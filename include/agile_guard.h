@@ -553,9 +553,13 @@ typedef struct {
  * (and every generic-space one that resolves to global) insert the guard sequence for
  * `policy`; functions named in opts->skip stay unguarded. The table address comes from
  * a module-scope `.global .u64 __agile_guard_table` and the log from
- * `__agile_guard_log`, so kernel signatures do not change. Bulk/tensor copies and
- * other forms the guard cannot cover are rejected (PTX_UNSUPPORTED). *out (NUL
- * terminated, length *out_len) is freed with agile_free. Host only. */
+ * `__agile_guard_log`, so kernel signatures do not change. Entry functions count their
+ * denials in registers and merge them into the log before each ret and exit, so the log
+ * is complete once the kernel has finished; under TRAP, and in modules where a called
+ * function can exit the thread, each denial is merged as it happens. Input that already
+ * names `__ag` symbols or registers, bulk/tensor copies and other forms the guard cannot
+ * cover are rejected (PTX_UNSUPPORTED). *out (NUL terminated, length *out_len) is freed
+ * with agile_free. Host only. */
 AGILE_API int agile_guard_instrument_ptx(const char *ptx, size_t len, const agile_instrument_opts_t *opts,
                                char **out, size_t *out_len, agile_instrument_report_t *report);
 
