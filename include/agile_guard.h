@@ -86,6 +86,11 @@ enum {
 
 #define AGILE_NO_RANGE 0xFFFFFFFFu
 #define AGILE_LOG_BYTES 64          /* device bytes of one violation log, 16-byte aligned */
+/* Bounded violation list (agile_violation_list_attach): a header, then one entry per
+ * recorded violation. */
+#define AGILE_LIST_HEADER_BYTES 16
+#define AGILE_LIST_ENTRY_BYTES 32
+#define AGILE_LIST_BYTES(capacity) (AGILE_LIST_HEADER_BYTES + (size_t)(capacity) * AGILE_LIST_ENTRY_BYTES)
 #define AGILE_MAX_RANGES 0x3FFFFFFFu
 
 /* One range of the guard table: [base, base + size), owned by `kind`. `id` is the
@@ -232,6 +237,23 @@ AGILE_API int agile_violation_log_init(void *d_log, uint32_t client, void *strea
  * when count > 0 -- the poison policy's "fail at a later synchronization" (Sec. V-E) --
  * and AGILE_ERR_TIMEOUT when a kernel's bounded wait gave up. */
 AGILE_API int agile_violation_log_read(const void *d_log, agile_violation_record_t *h_out, void *stream);
+
+/* Attach a bounded violation list to a log (Sec. V-E: report counts or logs would-be
+ * violations): from then on every violation recorded in d_log -- by the batch checks, the
+ * hand-fused kernels, the batched launches and instrumented modules -- is also appended
+ * to d_list, until `capacity` entries are taken; later ones are only counted. d_list is a
+ * caller-owned device buffer of AGILE_LIST_BYTES(capacity) bytes, 16-byte aligned, with
+ * capacity >= 1. Call after agile_violation_log_init (which detaches any list), on the
+ * stream the kernels use; entries appear in the order the GPU takes them. */
+AGILE_API int agile_violation_list_attach(void *d_log, void *d_list, uint32_t capacity, void *stream);
+
+/* Wait for `stream` and read an attached list: *n_seen = violations recorded since the
+ * attach (appended or not), *n_out = min(n_seen, capacity, max) entries decoded into
+ * h_out (key, addr, width, verdict, site and range id as in the log's first record;
+ * client and status from the log; count 1). INVALID_ARG when d_log has no list or
+ * d_list is not the one attached. */
+AGILE_API int agile_violation_list_read(const void *d_log, const void *d_list, agile_violation_record_t *h_out,
+                                        size_t max, size_t *n_out, uint64_t *n_seen, void *stream);
 
 /* Self-test of the kernels' bounded waits (failure detection without a GPU fault). One
  * warp waits on an mbarrier that expects 16 bytes no copy will deliver -- the guard's

@@ -16,4 +16,5 @@ from .abi import (  # noqa: F401
     agile_irregular_launch_fastpath, agile_stream_launch_shape, FAST_PATHS,
     agile_module_load, agile_module_unload, agile_stream_launch, agile_strerror,
     agile_validate_args, agile_validate_dma, agile_version, agile_violation_log_init, agile_violation_log_read, lib,
+    agile_violation_list_attach, agile_violation_list_read, list_bytes,
     library_path, LOG_BYTES, NO_RANGE, VERDICTS, KINDS, POLICIES, OPS, IRREGULAR)

@@ -16,6 +16,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libagileguard.so")
 
 LOG_BYTES = 64
+LIST_HEADER_BYTES = 16
+LIST_ENTRY_BYTES = 32
+
+
+def list_bytes(capacity: int) -> int:
+    """Device bytes of a bounded violation list of `capacity` entries (AGILE_LIST_BYTES)."""
+    return LIST_HEADER_BYTES + capacity * LIST_ENTRY_BYTES
 NO_RANGE = 0xFFFFFFFF
 VERDICTS = ["ALLOW", "PROTECTED", "MMIO", "STRADDLE", "UNMAPPED", "INVALID", "NOT_EXACT"]
 KINDS = {"user": 0, "protected": 1, "mmio": 2}
@@ -121,6 +128,8 @@ _SIG = {
     "agile_validate_dma": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P]),
     "agile_violation_log_init": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
     "agile_violation_log_read": (ctypes.c_int, [_P, _P, _P]),
+    "agile_violation_list_attach": (ctypes.c_int, [_P, _P, ctypes.c_uint32, _P]),
+    "agile_violation_list_read": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
     "agile_guard_check_batch": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
     "agile_aperture_check_batch": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P, ctypes.c_size_t,
                                                   _P, _P, _P]),
@@ -368,6 +377,29 @@ def agile_violation_log_read(d_log, stream=None):
                 "agile_violation_log_read", ok=(0, 1, -10))
     return rc, ViolationRecord(r.key, r.addr, r.width, r.verdict, r.site, r.range_id, r.client,
                                r.status, r.count)
+
+
+def agile_violation_list_attach(d_log, d_list, capacity: int, stream=None) -> None:
+    """Attach a bounded violation list (d_list: >= list_bytes(capacity) device bytes) to an
+    initialized log."""
+    _check(lib().agile_violation_list_attach(_dptr(d_log), _dptr(d_list), capacity, _stream(stream)),
+           "agile_violation_list_attach")
+
+
+def agile_violation_list_read(d_log, d_list, max_entries: int | None = None, stream=None):
+    """Returns (records, n_seen): the list's entries as ViolationRecords, in the order the
+    GPU took their slots, and the violations recorded since the attach."""
+    if max_entries is None:
+        max_entries = (d_list.numel() * d_list.element_size() - LIST_HEADER_BYTES) // LIST_ENTRY_BYTES
+    buf = (_Record * max(1, max_entries))()
+    n_out = ctypes.c_size_t()
+    n_seen = ctypes.c_uint64()
+    _check(lib().agile_violation_list_read(_dptr(d_log), _dptr(d_list), buf, max_entries,
+                                           ctypes.byref(n_out), ctypes.byref(n_seen), _stream(stream)),
+           "agile_violation_list_read")
+    recs = [ViolationRecord(r.key, r.addr, r.width, r.verdict, r.site, r.range_id, r.client,
+                            r.status, r.count) for r in buf[:n_out.value]]
+    return recs, n_seen.value
 
 
 # ---------------------------------------------------------------- device checks

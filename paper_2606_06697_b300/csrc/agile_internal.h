@@ -60,6 +60,11 @@ int batch_launch_fresh(void *d_buf, size_t n_items, const agile_batch_config_t *
 
 // Remember the last CUDA error text for agile_strerror-style diagnostics.
 void set_cuda_error(int err, const char *where);
+
+// Logs with a bounded violation list attached through this library (kept on the host, so
+// that the batch checks can launch their per-access form, which appends every violation,
+// for those logs only); agile_violation_log_init forgets a log.
+bool log_has_list(const void *d_log);
 int sm_count();
 }  // namespace agile
 

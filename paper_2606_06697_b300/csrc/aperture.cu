@@ -55,6 +55,7 @@ __device__ __forceinline__ void note_first(LaneLog &ll, size_t i, uint32_t v, ui
                                            uint64_t a) {
     if (ll.cnt == 0) { ll.key = i; ll.info = agile::pack_info(0, v, w, rid); ll.addr = a; }
     ++ll.cnt;
+    agile::list_append(ll.log, i, agile::pack_info(0, v, w, rid), a);
 }
 
 template <int N, int VEC>
@@ -66,6 +67,7 @@ k_aperture_batch(const Apertures A, const uint64_t *__restrict__ addr,
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
     const size_t ngroups = n / VEC;
     LaneLog ll;
+    ll.log = log;
     for (size_t g = tid; g < ngroups; g += nthreads) {
         if constexpr (VEC == 8) {
             const uint4 *pa = reinterpret_cast<const uint4 *>(addr + g * 8);
@@ -176,8 +178,9 @@ extern "C" int agile_aperture_check_batch(const agile_range_t *h_ap, size_t n_ap
     if (n == 0) return AGILE_OK;
     if (d_addr == nullptr || d_width == nullptr || d_verdict == nullptr) return AGILE_ERR_INVALID_ARG;
     if (d_log != nullptr && ((uintptr_t)d_log & 15) != 0) return AGILE_ERR_ALIGN;
+    // the per-access form also when the log has a list, which it appends every denial to
     const bool vec = ((uintptr_t)d_addr & 15) == 0 && ((uintptr_t)d_width & 7) == 0 &&
-                     ((uintptr_t)d_verdict & 7) == 0;
+                     ((uintptr_t)d_verdict & 7) == 0 && !agile::log_has_list(d_log);
     LogDev *log = (LogDev *)d_log;
     cudaStream_t st = (cudaStream_t)stream;
     return vec ? launch_n<8>(A, d_addr, d_width, n, d_verdict, log, st)

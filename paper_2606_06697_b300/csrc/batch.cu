@@ -84,6 +84,7 @@ __device__ void irregular_tile(const TView &V, const agile_dev_table_t &T, const
     const size_t n = W.n, n4 = n >> 2;
     const size_t u1 = e1 >= n ? n4 : e1 >> 2;
     LaneLog ll;
+    ll.log = S.log;
     for (size_t u0 = (e0 >> 2) + 32 * (threadIdx.x >> 5); u0 < u1; u0 += 32 * kWarps)
         agile::irregular_group<KIND, GUARD, POLICY>(V, T, idx, base, out, u0, u1, ll, spans);
     if (e1 >= n && (n & 3) && (threadIdx.x >> 5) == kWarps - 1)
@@ -127,6 +128,7 @@ k_batch(BatchHdr *H, const agile_work_t *__restrict__ items, const uint64_t *__r
                 }
                 s_item = lo;
                 s_work = items[lo];
+                S.log = static_cast<LogDev *>(s_work.log);
                 if (s_work.table != nullptr) s_T = *static_cast<const agile_dev_table_t *>(s_work.table);
             }
         }

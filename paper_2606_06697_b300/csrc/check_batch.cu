@@ -262,7 +262,8 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     agile::block_log_flush(log, ll);
 }
 
-// Inputs not aligned for vector loads: one access per thread per step, full rule.
+// Inputs not aligned for vector loads, or a log with a bounded list: one access per
+// thread per step, full rule, every denial noted (and appended to the list).
 template <int MODE, bool C32>
 __global__ void __launch_bounds__(kThreads, 1)
 k_check_batch_scalar(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
@@ -272,6 +273,7 @@ k_check_batch_scalar(const agile_dev_table_t T, const uint64_t *__restrict__ add
     __shared__ unsigned long long s_bar;
     const TView V = agile::stage_table<MODE>(T, smem, &s_bar, log);
     LaneLog ll;
+    ll.log = log;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const uint64_t a = addr[i];
@@ -343,8 +345,9 @@ extern "C" int agile_guard_check_batch(const agile_dev_table_t *tbl, const uint6
     if (d_addr == nullptr || d_width == nullptr || d_verdict == nullptr) return AGILE_ERR_INVALID_ARG;
     if (d_log != nullptr && ((uintptr_t)d_log & 15) != 0) return AGILE_ERR_ALIGN;
     if (tbl->cmap == nullptr) return AGILE_ERR_INVALID_ARG;
+    // the per-access form also when the log has a list, which it appends every denial to
     const bool vec = ((uintptr_t)d_addr & 15) == 0 && ((uintptr_t)d_width & 7) == 0 &&
-                     ((uintptr_t)d_verdict & 7) == 0;
+                     ((uintptr_t)d_verdict & 7) == 0 && !agile::log_has_list(d_log);
     LogDev *log = (LogDev *)d_log;
     cudaStream_t st = (cudaStream_t)stream;
     return tbl->crange != nullptr ? launch_staged<true>(*tbl, d_addr, d_width, n, d_verdict, log, st, vec)

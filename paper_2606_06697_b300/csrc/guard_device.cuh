@@ -38,14 +38,35 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // Device log, AGILE_LOG_BYTES bytes, 16-byte aligned. Two 128-bit words are kept at their
 // lexicographic minimum by compare-and-swap: first = (key, info) and where = (key, addr),
 // so both hold the fields of the violation with the smallest key whatever the schedule.
+// `list` is the device address of an attached bounded list (0: none) and `list_next` the
+// list slots taken since it was attached.
 struct LogDev {
     unsigned long long first_key, first_info;
     unsigned long long where_key, where_addr;
     unsigned long long count;
     uint32_t client, status;
-    unsigned long long pad[2];
+    unsigned long long list, list_next;
 };
 static_assert(sizeof(LogDev) == AGILE_LOG_BYTES, "log layout");
+static_assert(AGILE_LIST_HEADER_BYTES == 16 && AGILE_LIST_ENTRY_BYTES == 32, "list layout");
+
+// Append one violation record to the log's bounded list, if one is attached: the slot
+// comes from list_next, and the entry {key, addr, info, 0} is written when the slot is
+// below the capacity in the list's header (later violations are only counted). Called on
+// violation paths only.
+__device__ __forceinline__ void list_append(LogDev *L, unsigned long long key,
+                                            unsigned long long info, unsigned long long addr) {
+    if (L == nullptr) return;
+    const unsigned long long list = L->list;
+    if (list == 0) return;
+    const unsigned long long slot = atomicAdd(&L->list_next, 1ull);
+    if (slot >= *reinterpret_cast<const unsigned long long *>(list)) return;
+    ulonglong2 *e = reinterpret_cast<ulonglong2 *>(list + AGILE_LIST_HEADER_BYTES +
+                                                   slot * AGILE_LIST_ENTRY_BYTES);
+    e[0] = make_ulonglong2(key, addr);
+    e[1] = make_ulonglong2(info, 0ull);
+}
+
 
 __host__ __device__ inline unsigned long long pack_info(uint32_t site, uint32_t verdict,
                                                         uint32_t width, uint32_t rid) {
@@ -233,14 +254,17 @@ __device__ inline void cas_min128(unsigned long long *p, unsigned long long k,
     atomicOr(status, AGILE_LOG_STATUS_TIMEOUT);
 }
 
-// Per-thread running minimum of the violations it has seen.
+// Per-thread running minimum of the violations it has seen; each is also appended to the
+// bounded list of `log`, when it has one.
 struct LaneLog {
     uint32_t cnt = 0;
     unsigned long long key = ~0ull, info = ~0ull, addr = 0;
+    LogDev *log = nullptr;
     __device__ __forceinline__ void note(unsigned long long k, unsigned long long i,
                                          unsigned long long a) {
         ++cnt;
         if (k < key || (k == key && i < info)) { key = k; info = i; addr = a; }
+        list_append(log, k, i, a);
     }
 };
 
@@ -428,10 +452,12 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     return V;
 }
 
-// Per-warp violation slots in shared memory, written only by slow paths.
+// Per-warp violation slots in shared memory, written only by slow paths, and the log
+// whose bounded list the slow paths append to.
 struct WarpSlots {
     unsigned long long key[32], info[32], addr[32];
     uint32_t cnt[32];
+    LogDev *log;
 };
 
 __device__ inline void slots_init(WarpSlots &S) {

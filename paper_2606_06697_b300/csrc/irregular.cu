@@ -27,6 +27,7 @@ k_irregular(const agile_dev_table_t T, const int64_t *__restrict__ idx, float *b
     const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
     const size_t n4 = n >> 2;
     LaneLog ll;
+    ll.log = log;
     for (size_t u0 = warp * 32; u0 < n4; u0 += nwarps * 32)      // warp-uniform trip count
         agile::irregular_group<KIND, GUARD, POLICY, FAST>(V, T, idx, base, out, u0, n4, ll, true);
     if (blockIdx.x == 0 && threadIdx.x < 32 && (n & 3))

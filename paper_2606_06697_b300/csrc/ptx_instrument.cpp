@@ -656,7 +656,7 @@ class Rewriter {
         if (!aperture_) g += class_map_test(W, L);
         g += inline_check("%__agd0", W, st.site) +
              "\tsetp.eq.u64 %__agp2, %__agt16, 0;\n"            // info 0: allowed
-             "\tselp.u32 %__agr2, 1, 0, %__agp2;\n";
+             "\tselp.u32 %__agr2, 1, 0, %__agp2;\n" + list_append();
         if (acc_fn_)   // a denial: count + 1, and keep the smaller (address, info)
             g += "\tsetp.eq.u32 %__agp2, %__agr2, 0;\n"
                  "\t@%__agp2 add.u32 %__agc, %__agc, 1;\n"
@@ -761,6 +761,29 @@ class Rewriter {
                "\tsetp.eq.and.u32 %__agp2, %__agr2, 1, %__agp2;\n"
                "\tmov.u32 %__agr2, 1;\n"
                "\t@%__agp2 bra " + L + ";\n";
+    }
+
+    // A denial (%__agp2 clear) appended to the log's bounded list when one is attached
+    // (log offsets 48: list, 56: slots taken; list header: capacity; entries of 32 bytes
+    // {address, address, info, 0} from byte 16), while a slot below the capacity is left.
+    std::string list_append() {
+        const std::string E = "$__AG_LS_" + std::to_string(label_++);
+        return "\t@%__agp2 bra " + E + ";\n"
+               "\tld.global.u64 %__agt2, [__agile_guard_log];\n"
+               "\tsetp.eq.u64 %__agq0, %__agt2, 0;\n"
+               "\t@%__agq0 bra " + E + ";\n"
+               "\tld.global.u64 %__agt3, [%__agt2+48];\n"
+               "\tsetp.eq.u64 %__agq0, %__agt3, 0;\n"
+               "\t@%__agq0 bra " + E + ";\n"
+               "\tatom.global.add.u64 %__agt4, [%__agt2+56], 1;\n"
+               "\tld.global.u64 %__agt5, [%__agt3];\n"
+               "\tsetp.ge.u64 %__agq0, %__agt4, %__agt5;\n"
+               "\t@%__agq0 bra " + E + ";\n"
+               "\tshl.b64 %__agt4, %__agt4, 5;\n"
+               "\tadd.s64 %__agt4, %__agt4, %__agt3;\n"
+               "\tmov.b64 %__agt5, 0;\n"
+               "\tst.global.v2.u64 [%__agt4+16], {%__agd0, %__agd0};\n"
+               "\tst.global.v2.u64 [%__agt4+32], {%__agt16, %__agt5};\n" + E + ":\n";
     }
 
     // Effective address [base + off] into register `dst`.

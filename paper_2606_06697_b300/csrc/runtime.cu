@@ -7,6 +7,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <mutex>
+#include <unordered_set>
 
 #include "agile_internal.h"
 #include "guard_device.cuh"
@@ -14,6 +15,14 @@
 namespace {
 
 thread_local char g_cuda_msg[256] = "";
+
+std::mutex g_list_mu;
+std::unordered_set<const void *> g_listed;      // logs with a list attached
+
+void set_listed(const void *d_log, bool on) {
+    std::lock_guard<std::mutex> g(g_list_mu);
+    if (on) g_listed.insert(d_log); else g_listed.erase(d_log);
+}
 
 __global__ void k_log_init(agile::LogDev *L, uint32_t client) {
     if (threadIdx.x == 0) {
@@ -24,7 +33,8 @@ __global__ void k_log_init(agile::LogDev *L, uint32_t client) {
         L->count = 0;
         L->client = client;
         L->status = 0;
-        L->pad[0] = L->pad[1] = 0;
+        L->list = 0;
+        L->list_next = 0;
     }
 }
 
@@ -35,6 +45,12 @@ namespace agile {
 void set_cuda_error(int err, const char *where) {
     std::snprintf(g_cuda_msg, sizeof g_cuda_msg, "%s: %s", where,
                   cudaGetErrorString((cudaError_t)err));
+}
+
+bool log_has_list(const void *d_log) {
+    if (d_log == nullptr) return false;
+    std::lock_guard<std::mutex> g(g_list_mu);
+    return g_listed.count(d_log) != 0;
 }
 
 int sm_count() {
@@ -60,6 +76,7 @@ int agile_violation_log_init(void *d_log, uint32_t client, void *stream) {
     if (d_log == nullptr || ((uintptr_t)d_log & 15) != 0) return AGILE_ERR_ALIGN;
     k_log_init<<<1, 32, 0, (cudaStream_t)stream>>>((agile::LogDev *)d_log, client);
     AGILE_CUDA_TRY(cudaGetLastError());
+    set_listed(d_log, false);
     return AGILE_OK;
 }
 
@@ -83,6 +100,67 @@ int agile_violation_log_read(const void *d_log, agile_violation_record_t *h_out,
     }
     if (L.status & AGILE_LOG_STATUS_TIMEOUT) return AGILE_ERR_TIMEOUT;
     return L.count ? AGILE_VIOLATION : AGILE_OK;
+}
+
+int agile_violation_list_attach(void *d_log, void *d_list, uint32_t capacity, void *stream) {
+    if (d_log == nullptr || d_list == nullptr || capacity == 0) return AGILE_ERR_INVALID_ARG;
+    if (((uintptr_t)d_log & 15) != 0 || ((uintptr_t)d_list & 15) != 0) return AGILE_ERR_ALIGN;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the list's header (its capacity), then the log's list address and slot counter;
+    // the stream is synchronized before the host words go out of scope
+    const unsigned long long h_hdr[2] = {capacity, 0};
+    const unsigned long long h_ref[2] = {(unsigned long long)(uintptr_t)d_list, 0};
+    agile::LogDev *L = (agile::LogDev *)d_log;
+    AGILE_CUDA_TRY(cudaMemcpyAsync(d_list, h_hdr, sizeof h_hdr, cudaMemcpyHostToDevice, st));
+    AGILE_CUDA_TRY(cudaMemcpyAsync(&L->list, h_ref, sizeof h_ref, cudaMemcpyHostToDevice, st));
+    AGILE_CUDA_TRY(cudaStreamSynchronize(st));
+    set_listed(d_log, true);
+    return AGILE_OK;
+}
+
+int agile_violation_list_read(const void *d_log, const void *d_list, agile_violation_record_t *h_out,
+                              size_t max, size_t *n_out, uint64_t *n_seen, void *stream) {
+    if (d_log == nullptr || d_list == nullptr || n_out == nullptr || n_seen == nullptr ||
+        (h_out == nullptr && max > 0))
+        return AGILE_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    agile::LogDev L;
+    unsigned long long hdr[2];
+    AGILE_CUDA_TRY(cudaMemcpyAsync(&L, d_log, sizeof L, cudaMemcpyDeviceToHost, st));
+    AGILE_CUDA_TRY(cudaMemcpyAsync(hdr, d_list, sizeof hdr, cudaMemcpyDeviceToHost, st));
+    AGILE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (L.list != (unsigned long long)(uintptr_t)d_list) return AGILE_ERR_INVALID_ARG;
+    const unsigned long long taken = L.list_next < hdr[0] ? L.list_next : hdr[0];
+    const size_t m = taken < max ? (size_t)taken : max;
+    *n_seen = L.list_next;
+    *n_out = m;
+    if (m == 0) return AGILE_OK;
+    unsigned long long *e = static_cast<unsigned long long *>(std::malloc(m * AGILE_LIST_ENTRY_BYTES));
+    if (e == nullptr) return AGILE_ERR_NOMEM;
+    cudaError_t rc = cudaMemcpyAsync(e, static_cast<const unsigned char *>(d_list) + AGILE_LIST_HEADER_BYTES,
+                                     m * AGILE_LIST_ENTRY_BYTES, cudaMemcpyDeviceToHost, st);
+    if (rc == cudaSuccess) rc = cudaStreamSynchronize(st);
+    if (rc != cudaSuccess) {
+        std::free(e);
+        agile::set_cuda_error(rc, "agile_violation_list_read");
+        return AGILE_ERR_CUDA;
+    }
+    for (size_t j = 0; j < m; ++j) {
+        const unsigned long long *x = e + 4 * j;            // {key, addr, info, 0}
+        agile_violation_record_t &r = h_out[j];
+        std::memset(&r, 0, sizeof r);
+        r.key = x[0];
+        r.addr = x[1];
+        r.site = (uint32_t)(x[2] >> 48) & 0xFFFFu;
+        r.verdict = (uint32_t)(x[2] >> 40) & 0xFFu;
+        r.width = (uint32_t)(x[2] >> 32) & 0xFFu;
+        r.range_id = (uint32_t)x[2];
+        r.client = L.client;
+        r.status = L.status;
+        r.count = 1;
+    }
+    std::free(e);
+    return AGILE_OK;
 }
 
 void agile_free(void *p) { std::free(p); }

@@ -30,6 +30,7 @@ k_stream(const agile_dev_table_t T, float *__restrict__ a, const float *__restri
         // The page map is read through L1 rather than staged: a warp checks three spans
         // per tile, and skipping the staging lets every block start streaming at once.
         agile::slots_init(S);
+        if (threadIdx.x == 0) S.log = log;
         __syncthreads();
         V = agile::view_of(T);
     }

@@ -55,6 +55,7 @@ static __device__ __noinline__ void slow_tile(const TView &V, const agile_dev_ta
     constexpr bool kAlways = POLICY == AGILE_POLICY_REPORT;
     const uint32_t lane = threadIdx.x & 31;
     LaneLog ll;
+    ll.log = S.log;
     if constexpr (!TAIL) {
         const float4 *b4 = reinterpret_cast<const float4 *>(b);
         const float4 *c4 = reinterpret_cast<const float4 *>(c);

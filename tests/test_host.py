@@ -35,6 +35,23 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == exported
 
 
+def test_violation_list_arguments():
+    """The bounded list's size formula and its argument checks, which run before any CUDA
+    call."""
+    import ctypes
+    assert ag.list_bytes(0) == 16 and ag.list_bytes(3) == 16 + 3 * 32
+    L = ag.lib()
+    assert L.agile_violation_list_attach(None, None, 4, None) == -1          # no log
+    assert L.agile_violation_list_attach(0x1000, 0x2000, 0, None) == -1      # capacity 0
+    assert L.agile_violation_list_attach(0x1008, 0x2000, 4, None) == -12     # log alignment
+    assert L.agile_violation_list_attach(0x1000, 0x2008, 4, None) == -12     # list alignment
+    n_out, n_seen = ctypes.c_size_t(), ctypes.c_uint64()
+    assert L.agile_violation_list_read(None, 0x2000, None, 0, ctypes.byref(n_out),
+                                       ctypes.byref(n_seen), None) == -1
+    assert L.agile_violation_list_read(0x1000, 0x2000, None, 4, ctypes.byref(n_out),
+                                       ctypes.byref(n_seen), None) == -1      # no room given
+
+
 def test_strerror_and_version():
     assert ag.agile_version() == 0x000100
     assert "overlap" in ag.agile_strerror(-2)
