@@ -186,3 +186,39 @@ def test_list_ptx_merged_at_every_exit():
     exp = expected(addr, np.full(len(addr), 4, np.uint8), sites, key_is_index=False, r=r)
     assert rec.count == sum(exp.values())
     check(recs, n_seen, exp, 4096)
+
+
+def test_list_batched_clients():
+    """Many clients in one persistent launch, each log with a list of its own: every
+    client's list holds the same multiset as when the client ran alone (whose count and
+    first record the oracle fixes in the batched-launch tests)."""
+    from paper_2606_06697_b300.clients import ClientSet
+    from test_gpu_batch_clients import small_specs
+    cs = ClientSet(small_specs(), DEV, log2_pages=(21,), frac_bad=0.01, policy="poison")
+    n = len(cs.clients)
+    cap = 1 << 14
+    lists = [torch.zeros(ag.list_bytes(cap), dtype=torch.uint8, device=DEV) for _ in range(n)]
+
+    def attach_all():
+        for i in range(n):
+            ag.agile_violation_list_attach(cs.log(i), lists[i], cap)
+
+    cs.reset()
+    attach_all()
+    for i in range(n):
+        cs.run_single(i, 0)
+    alone = []
+    for i in range(n):
+        recs, seen = ag.agile_violation_list_read(cs.log(i), lists[i])
+        _, rec = ag.agile_violation_log_read(cs.log(i))
+        assert seen == rec.count == len(recs)
+        alone.append(entries(recs))
+    assert sum(sum(e.values()) for e in alone) > 0
+    buf = torch.empty(ag.agile_batch_device_bytes(n), dtype=torch.uint8, device=DEV)
+    cs.reset()
+    attach_all()
+    ag.agile_batch_upload(cs.work(0), 4096, buf)
+    ag.agile_batch_launch(buf, n, 4096, True, 2)
+    for i in range(n):
+        recs, seen = ag.agile_violation_list_read(cs.log(i), lists[i])
+        assert seen == sum(alone[i].values()) and entries(recs) == alone[i], i
