@@ -272,7 +272,8 @@ AGILE_API int agile_selftest_bounded_waits(void *d_log, const uint32_t *d_flag, 
  * kernel guard applies it (Sec. V-E). Violations go to d_log (first fault = smallest
  * index) when d_log is not NULL. Layout: SoA, n entries each; any alignment is
  * accepted (16-byte aligned d_addr and 8-byte aligned d_width/d_verdict take the
- * vector path). A violation is not an error: returns 0 once queued. */
+ * vector path, unless d_log has a bounded list attached: the per-access path then runs,
+ * which appends every denial). A violation is not an error: returns 0 once queued. */
 AGILE_API int agile_guard_check_batch(const agile_dev_table_t *tbl, const uint64_t *d_addr,
                             const uint8_t *d_width, size_t n, uint8_t *d_verdict, void *d_log,
                             void *stream);
