@@ -8,10 +8,16 @@
 // bulk and tensor copies (cp.*), asynchronous stores/reductions, multimem, surfaces,
 // tensormap and discard -- are rejected (fail closed, Sec. IV-C).
 //
-// The inserted sequence, per access of W bytes at effective address a:
-//   fast path (inline): page p = (a - lo) >> log2 G; allowed at once when p is in the
-//   window, the page map entry says all-user, and (a - lo) mod G + W <= G;
-//   slow path: call __agile_guard_check(a, W, site) -- full classification, log on deny;
+// The inserted sequence, per access of W bytes at effective address a, in program order:
+//   1. inline bitmap test: the all-user bitmap's word for a's block, and the first and
+//      last byte of the access in the same block;
+//   2. when the bitmap block is mixed, inline class-map test: a's block in the 2-bit block
+//      class map is class 1 (inside one user range) and holds the whole access;
+//   3. only then the slow path, inlined with labels of its own: the page map, else the
+//      binary search over the page's ranges and the walk (full classification). A
+//      denial is appended to the log's bounded list when one is attached, and counted:
+//      in the registers of an entry function (merged per warp by __agile_guard_flush
+//      before each ret and exit), else merged into the log at once;
 //   then the policy: POISON/SINK send a denied load to the zero page; POISON predicates
 //   a denied store/atom/red off (a denied atom's result reads 0), SINK sends it to the
 //   sink page; REPORT changes nothing; TRAP emits `@!ok trap;`.
