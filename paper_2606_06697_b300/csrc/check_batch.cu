@@ -125,9 +125,13 @@ __device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32
         const uint64_t m = (1ull << V.clg) - 1;
         ok = (off & m) + w <= m + 1;
     }
-    // 16 codes per word: rotating the word by 2 * blk (mod 32) brings this block's to bit 0
+    // 16 codes per word: rotating the word by 2 * blk (mod 32) brings this block's to bit 0.
+    // The doubling is a multiply, so that it issues on the FMA pipe: pass 1 is bound by
+    // the integer ALU pipe while the FMA pipe idles.
     const uint32_t word = V.cmap[blk >> 4];
-    const uint32_t code = __funnelshift_r(word, word, blk * 2u) & 3u;
+    uint32_t sh;
+    asm("mul.lo.u32 %0, %1, 2;" : "=r"(sh) : "r"(blk));
+    const uint32_t code = __funnelshift_r(word, word, sh) & 3u;
     return ok && legal_width(w) ? code : 0u;
 }
 
@@ -184,8 +188,10 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             // and 1 (user) give ALLOW, 2 (hole) UNMAPPED, 3 (protected) PROTECTED.
             uint32_t sel = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                sel += cmap_code<C32>(V, av[k], (uint32_t)(wv >> (8 * k)) & 0xFFu) << (4 * k);
+            for (int k = 0; k < 8; ++k) {           // sel += code << 4k, as a multiply-add (FMA pipe)
+                const uint32_t cd = cmap_code<C32>(V, av[k], (uint32_t)(wv >> (8 * k)) & 0xFFu);
+                asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(sel) : "r"(cd), "r"(1u << (4 * k)));
+            }
             const uint32_t vlo = __byte_perm(0x01040000u, 0u, sel);
             const uint32_t vhi = __byte_perm(0x01040000u, 0u, sel >> 16);
             __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8),
