@@ -142,10 +142,11 @@ typedef struct {
                                    3  the block lies inside one protected range
                                    0  anything else (MMIO, several ranges, a boundary)
                                  C is the smallest power of two >= 256 bytes that keeps the
-                                 map at 2^19 blocks (128 KiB) or fewer; cmap_n + 1 blocks,
-                                 the last always 0. Used by the batch check to decide most
-                                 accesses, denied ones included, from one 2-bit code, and
-                                 by the PTX pass's second inline test (class 1 allows). */
+                                 map at 2^19 blocks (128 KiB) or fewer; cmap_n + 1 entries,
+                                 the last always 2: nothing lies outside the window. Used
+                                 by the batch check to decide most accesses, denied ones
+                                 included, from one 2-bit code, and by the PTX pass's
+                                 second inline test (class 1 allows).                   */
     uint32_t cmap_log2;
     uint32_t cmap_n;          /* blocks covering the window                             */
 } agile_dev_table_t;

@@ -12,7 +12,8 @@
 // Pass 1 decides each access from its block's 2-bit class alone, without branches: an
 // access inside one block of class user, hole or protected gets ALLOW, UNMAPPED or
 // PROTECTED. The rest -- blocks holding a boundary, MMIO blocks, accesses that cross a
-// block edge or lie outside the window, illegal widths -- are "open". Pass 2 deals the
+// block edge, lie below the window in 32-bit mode, illegal widths -- are "open"; accesses
+// wholly beyond the window read its last entry, "unmapped". Pass 2 deals the
 // warp's open accesses out over its lanes, 32 at a time, and decides each by the full
 // rule (the 32-bit uniform decision over the packed records where it applies). Each
 // thread keeps its smallest violation in registers; the block reduces them once at the
@@ -116,7 +117,7 @@ __device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32
     if constexpr (C32) {
         const uint32_t o = (uint32_t)off;
         const uint32_t k = o >> V.clg;
-        blk = k < V.cn ? k : V.cn;                     // past the window: the open entry
+        blk = k < V.cn ? k : V.cn;                     // past the window: its "unmapped" entry
         const uint32_t m = (1u << V.clg) - 1u;
         ok = (off >> 32) == 0 && (o & m) + w <= m + 1u;
     } else {

@@ -63,9 +63,10 @@ void build_pages(agile_guard_table &t) {
 
 // Class of every block of C = 2^cmap_log2 bytes from lo: 1 inside one user range, 3 inside
 // one protected range, 2 touched by no range, 0 otherwise (an MMIO block, a block holding a
-// range boundary, and the always-open entry past the last block). A block that ends at
-// 2^64 stays 0, so an access ending there reaches the full rule, which finds its end
-// unrepresentable.
+// range boundary). The entry past the last block is 2: every range lies inside the
+// window, so an access wholly beyond the map's end, or wholly below lo (its offset wraps),
+// touches none. A block that ends at 2^64 stays 0, so an access ending there reaches the
+// full rule, which finds its end unrepresentable.
 void build_cmap(const agile_guard_table &t, uint32_t *map, uint64_t window) {
     const uint64_t C = 1ull << t.cmap_log2, nb = t.cmap_n;
     auto set = [&](uint64_t k, uint32_t code) {
@@ -82,7 +83,7 @@ void build_cmap(const agile_guard_table &t, uint32_t *map, uint64_t window) {
         if (k0 < f0) set(k0, 0);                                      // partial first block
         if (k1 >= f1 && k1 < nb) set(k1, 0);                          // partial last block
     }
-    set(nb, 0);
+    set(nb, 2);
     if (window != 0 && t.lo + window == 0 && nb > 0) set(nb - 1, 0);  // window ends at 2^64
 }
 

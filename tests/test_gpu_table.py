@@ -52,8 +52,8 @@ def test_ubits_match_bruteforce(log2_page):
 
 def block_classes(r, lo, lg, nblocks):
     """Class of each block from the sorted ranges: 1 inside one user range, 3 inside one
-    protected range, 2 touched by no range, 0 otherwise, for the block that ends at 2^64,
-    and for the entry past the last block. Offsets are taken from lo in uint64."""
+    protected range, 2 touched by no range, 0 otherwise and for the block that ends at
+    2^64; the entry past the last block is 2. Offsets are taken from lo in uint64."""
     o = np.argsort(r.base)
     rb = (r.base[o] - np.uint64(lo)).astype(np.uint64)
     re = rb + r.size[o].astype(np.uint64)
@@ -70,7 +70,7 @@ def block_classes(r, lo, lg, nblocks):
     want[full & (kind[j] == syn.KIND_USER)] = 1
     want[full & (kind[j] == syn.KIND_PROTECTED)] = 3
     want[s1 > np.uint64(2**64 - 1 - lo)] = 0            # ends at (or past) 2^64
-    return np.concatenate([want, [0]]).astype(np.uint8)
+    return np.concatenate([want, [2]]).astype(np.uint8)
 
 
 @pytest.mark.parametrize("log2_page", [12, 21])
