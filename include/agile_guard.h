@@ -245,7 +245,8 @@ AGILE_API int agile_violation_log_read(const void *d_log, agile_violation_record
  * to d_list, until `capacity` entries are taken; later ones are only counted. d_list is a
  * caller-owned device buffer of AGILE_LIST_BYTES(capacity) bytes, 16-byte aligned, with
  * capacity >= 1. Call after agile_violation_log_init (which detaches any list), on the
- * stream the kernels use; entries appear in the order the GPU takes them. */
+ * stream the kernels use; synchronous (it waits for that stream). Entries appear in the
+ * order the GPU takes them. */
 AGILE_API int agile_violation_list_attach(void *d_log, void *d_list, uint32_t capacity, void *stream);
 
 /* Wait for `stream` and read an attached list: *n_seen = violations recorded since the
