@@ -105,10 +105,11 @@ __device__ __forceinline__ bool legal_width(uint32_t w) {
 }
 
 // Pass-1 class of one access from the block class map: the 2-bit code of its block (1
-// user, 2 hole, 3 protected) when the access is decided here -- it lies inside that block,
-// inside the window, and has a legal width -- else 0 ("open": the block holds a boundary
-// or MMIO, the access crosses the block's end, lies outside the window, or has an illegal
-// width). C32: the window spans under 4 GiB, so block index and offset are 32-bit.
+// user, 2 hole, 3 protected) when the access is decided here -- it lies inside that block
+// and has a legal width; an access wholly beyond the window reads the map's last entry, 2
+// -- else 0 ("open": the block holds a boundary or MMIO, the access crosses the block's
+// end, lies below the window in 32-bit mode, or has an illegal width). C32: the window
+// spans under 4 GiB, so block index and offset are 32-bit.
 template <bool C32>
 __device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32_t w) {
     const uint64_t off = a - V.lo;
@@ -119,7 +120,12 @@ __device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32
         const uint32_t k = o >> V.clg;
         blk = k < V.cn ? k : V.cn;                     // past the window: its "unmapped" entry
         const uint32_t m = (1u << V.clg) - 1u;
-        ok = (off >> 32) == 0 && (o & m) + w <= m + 1u;
+        // An illegal width gets 2^30 added (a multiply-add, FMA pipe), so that it fails the
+        // in-block test: blocks are at most 2^13 bytes here, and the sum cannot wrap.
+        const uint32_t bad = ~shr_clamped(0x10116u, w) & 1u;
+        uint32_t wf;
+        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(wf) : "r"(bad), "r"(1u << 30), "r"(w));
+        ok = (off >> 32) == 0 && (o & m) + wf <= m + 1u;
     } else {
         const uint64_t k = off >> V.clg;
         blk = k < V.cn ? (uint32_t)k : V.cn;
@@ -133,6 +139,7 @@ __device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32
     uint32_t sh;
     asm("mul.lo.u32 %0, %1, 2;" : "=r"(sh) : "r"(blk));
     const uint32_t code = __funnelshift_r(word, word, sh) & 3u;
+    if constexpr (C32) return ok ? code : 0u;           // illegal widths failed above
     return ok && legal_width(w) ? code : 0u;
 }
 
