@@ -197,7 +197,10 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             uint32_t sel = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {           // sel += code << 4k, as a multiply-add (FMA pipe)
-                const uint32_t cd = cmap_code<C32>(V, av[k], (uint32_t)(wv >> (8 * k)) & 0xFFu);
+                // width byte k by one byte permute
+                const uint32_t wk = __byte_perm(k < 4 ? (uint32_t)wv : (uint32_t)(wv >> 32), 0u,
+                                                0x4440u | (uint32_t)(k & 3));
+                const uint32_t cd = cmap_code<C32>(V, av[k], wk);
                 asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(sel) : "r"(cd), "r"(1u << (4 * k)));
             }
             const uint32_t vlo = __byte_perm(0x01040000u, 0u, sel);
@@ -234,9 +237,8 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             const uint32_t omask = __shfl_sync(agile::kFull, open, own & 31);
             const uint32_t oexcl = __shfl_sync(agile::kFull, excl, own & 31);
             if (q < total) {
-                uint32_t m = omask;
-                for (uint32_t r = q - oexcl; r; --r) m &= m - 1;   // drop the earlier ones
-                const int b = __ffs(m) - 1;                       // bit 4k + h
+                // bit 4k + h: the owner's (q - oexcl + 1)-th open access
+                const int b = (int)__fns(omask, 0, (int)(q - oexcl) + 1);
                 const size_t i = (g0 + 32 * (b & 3) + own) * 8 + (b >> 2);
                 const uint64_t a = addr[i];
                 const uint32_t w = width[i];
