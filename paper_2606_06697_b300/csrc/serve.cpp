@@ -34,6 +34,18 @@
 
 namespace {
 
+// A short busy wait that keeps the core: the worker's latency-critical loop must not give
+// its core away for a scheduler tick while launches are in flight or an arrival is near.
+inline void spin_pause() {
+    for (int i = 0; i < 16; ++i) {
+#if defined(__x86_64__) || defined(__i386__)
+        __builtin_ia32_pause();
+#elif defined(__aarch64__)
+        asm volatile("yield");
+#endif
+    }
+}
+
 // A slot's device region: the batch work list of n requests (header, items, tile prefix
 // sums), directly followed by one u32 done counter per request, so one copy carries both.
 size_t list_bytes(size_t n) { return 64 + 64 * n + 8 * (n + 1); }
@@ -86,6 +98,8 @@ struct agile_worker {
     std::unordered_set<uint64_t> busy_keys;
     uint64_t admitted = 0;
     uint32_t launches = 0;
+    std::vector<uint32_t> batch_buf;             // launch(): reused, so a launch allocates nothing
+    std::unordered_set<uint64_t> keys_buf;
 
     uint64_t now() const {
         return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -190,8 +204,10 @@ struct agile_worker {
 
     void launch(Slot &s, uint64_t t) {
         if (!cfg.continuous && any_busy()) return;
-        std::vector<uint32_t> batch;
-        std::unordered_set<uint64_t> keys;
+        std::vector<uint32_t> &batch = batch_buf;
+        std::unordered_set<uint64_t> &keys = keys_buf;
+        batch.clear();
+        keys.clear();
         uint64_t mem = 0;
         for (auto it = waiting.begin(); it != waiting.end() && batch.size() < cfg.max_batch;) {
             const agile_request_t &r = reqs[*it];
@@ -237,7 +253,7 @@ struct agile_worker {
         admitted += mem;
         admitted_pub.store(admitted);
         if (admitted > peak_pub.load()) peak_pub.store(admitted);
-        s.reqs = std::move(batch);
+        s.reqs.assign(batch.begin(), batch.end());
         s.fin.assign(n, 0);
         s.open = (uint32_t)n;
         if (!launched || !recorded) {
@@ -280,7 +296,7 @@ struct agile_worker {
                 continue;
             }
             if (any_busy()) {
-                std::this_thread::yield();
+                spin_pause();
             } else if (!arrivals.empty()) {
                 // Sleep only through long gaps, waking 1 ms early: a sleep can overrun by
                 // tens of microseconds, which would land on the request's latency. The
@@ -288,7 +304,7 @@ struct agile_worker {
                 const uint64_t next = arrivals.top().first;
                 const uint64_t t2 = now();
                 if (next > t2 + 1500000) std::this_thread::sleep_for(std::chrono::nanoseconds(next - t2 - 1000000));
-                else std::this_thread::yield();
+                else spin_pause();
             } else {
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
             }
@@ -327,9 +343,13 @@ int agile_worker_create(const agile_worker_config_t *cfg, const agile_guard_tabl
     cudaGetDevice(&w->device);
     const size_t sb = slot_bytes(cfg->max_batch);
     w->slots.resize(cfg->max_inflight);
+    w->batch_buf.reserve(cfg->max_batch);
+    w->keys_buf.reserve(2 * (size_t)cfg->max_batch);
     for (uint32_t k = 0; k < cfg->max_inflight; ++k) {
         Slot &s = w->slots[k];
         s.dev = static_cast<unsigned char *>(d_buf) + k * sb;
+        s.reqs.reserve(cfg->max_batch);
+        s.fin.reserve(cfg->max_batch);
         cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.staging), sb);
