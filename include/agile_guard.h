@@ -149,6 +149,23 @@ typedef struct {
                                  second inline test (class 1 allows).                   */
     uint32_t cmap_log2;
     uint32_t cmap_n;          /* blocks covering the window                             */
+    const uint32_t *cdesc;    /* windows under 4 GiB: descriptors of open blocks (class 0)
+                                 for the batch check's second pass, else NULL. A block
+                                 with at most one range boundary strictly inside it (none:
+                                 inside one MMIO range) is described by a pair of u32
+                                 {block index, payload}: the boundary's offset b in the
+                                 block (C when there is none) in bits 0-13, and the
+                                 verdicts of an access wholly before b, wholly at or after
+                                 b, and across b in bits 16-18, 20-22, 24-26. Pairs sit in
+                                 2^cdesc_log2 slots, block k in slot h(k, cdesc_k1) or
+                                 h(k, cdesc_k2), h(k, K) = (k * K mod 2^32) >> (32 -
+                                 cdesc_log2); an empty slot holds block 0xFFFFFFFF. Blocks
+                                 left out (more boundaries, or no free slot) are decided
+                                 by the full rule.                                      */
+    uint32_t cdesc_log2;      /* 6..12 when cdesc is not NULL                           */
+    uint32_t cdesc_k1;
+    uint32_t cdesc_k2;
+    uint32_t cdesc_reserved;
 } agile_dev_table_t;
 
 /* Decoded violation log. The first fault is the violating access with the smallest

@@ -54,7 +54,9 @@ class _DevTable(ctypes.Structure):
                 ("remap_or", ctypes.c_uint64), ("ubits", ctypes.c_void_p),
                 ("ubits_log2", ctypes.c_uint32), ("ubits_n", ctypes.c_uint32),
                 ("cmap", ctypes.c_void_p), ("cmap_log2", ctypes.c_uint32),
-                ("cmap_n", ctypes.c_uint32)]
+                ("cmap_n", ctypes.c_uint32), ("cdesc", ctypes.c_void_p),
+                ("cdesc_log2", ctypes.c_uint32), ("cdesc_k1", ctypes.c_uint32),
+                ("cdesc_k2", ctypes.c_uint32), ("cdesc_reserved", ctypes.c_uint32)]
 
 
 class _Record(ctypes.Structure):

@@ -28,6 +28,8 @@ struct agile_guard_table {
     size_t off_cmap = 0;                  // block class map (2 bits per block)
     uint32_t cmap_log2 = 8;
     uint32_t cmap_n = 0;
+    size_t off_cdesc = 0;                 // open-block descriptors (windows under 4 GiB)
+    uint32_t cdesc_log2 = 0, cdesc_k1 = 0, cdesc_k2 = 0;
 };
 
 namespace agile {

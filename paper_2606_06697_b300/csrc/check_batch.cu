@@ -14,10 +14,13 @@
 // PROTECTED. The rest -- blocks holding a boundary, MMIO blocks, accesses that cross a
 // block edge, lie below the window in 32-bit mode, illegal widths -- are "open"; accesses
 // wholly beyond the window read its last entry, "unmapped". Pass 2 deals the
-// warp's open accesses out over its lanes, 32 at a time, and decides each by the full
-// rule (the 32-bit uniform decision over the packed records where it applies). Each
-// thread keeps its smallest violation in registers; the block reduces them once at the
-// end.
+// warp's open accesses out over its lanes, 32 at a time. Where the table has open-block
+// descriptors (windows under 4 GiB), an access inside a described block is decided from
+// its block's descriptor: one boundary and three verdicts. The rest go to a per-warp
+// queue in shared memory, and each time it holds 32 of them the warp decides those 32
+// by the full rule (the 32-bit uniform decision over the packed records where it
+// applies). Each thread keeps its smallest violation in registers; the block reduces
+// them once at the end.
 #include <cuda_runtime.h>
 
 #include "agile_internal.h"
@@ -143,6 +146,24 @@ __device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32
     return ok && legal_width(w) ? code : 0u;
 }
 
+// Pass-2 decision from the open-block descriptors (windows under 4 GiB): false when the
+// access's block has no descriptor, or the access is not inside one block of the window
+// with a legal width. Branch-free: both slots of the two-choice hash are read.
+__device__ __forceinline__ bool desc_decide(const TView &V, uint64_t a, uint32_t w, uint32_t *v) {
+    const uint64_t off = a - V.lo;
+    const uint32_t o = (uint32_t)off;
+    const uint32_t k = o >> V.clg;
+    const uint32_t oi = o & ((1u << V.clg) - 1u), e = oi + w;
+    const uint32_t sh = 32u - V.dlg;                   // dlg >= 6
+    const uint2 d1 = V.cdesc[(k * V.dk1) >> sh], d2 = V.cdesc[(k * V.dk2) >> sh];
+    const bool hit = d1.x == k || d2.x == k;
+    const uint32_t p = d1.x == k ? d1.y : d2.y;
+    const uint32_t b = p & 0x3FFFu;                    // the boundary, C when none
+    const uint32_t f = e <= b ? 16u : oi >= b ? 20u : 24u;   // before, at or after, across
+    *v = (p >> f) & 7u;
+    return hit && (off >> 32) == 0 && e <= (1u << V.clg) && legal_width(w);
+}
+
 // Full rule for one access (pass 2, the n mod 8 tail, and the misaligned form).
 template <bool C32>
 __device__ __forceinline__ uint32_t full_rule(const TView &V, uint64_t a, uint32_t w, uint32_t *rid) {
@@ -157,6 +178,14 @@ __device__ __forceinline__ uint32_t full_rule(const TView &V, uint64_t a, uint32
     }
 }
 
+// Per-warp queue of open accesses the descriptors left undecided: fewer than 32 wait
+// between rounds, and a round adds at most 32. An entry holds the access itself (its
+// index with the width in the top byte, and its address), so that deciding it later
+// does not read the inputs again: by then they may have left L2.
+constexpr uint32_t kQueue = 64;
+constexpr uint32_t kQueueBytes = kThreads / 32 * kQueue * 16;
+constexpr uint64_t kIndexMask = (1ull << 56) - 1;   // indices below 2^56
+
 template <int MODE, bool C32, int kG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
@@ -165,12 +194,26 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_bar;
     const TView V = agile::stage_table<MODE>(T, smem, &s_bar, log);
+    constexpr bool kDesc = C32 && (MODE & agile::ST_CDESC);
+    // the queue follows the staged sections
+    ulonglong2 *s_q = reinterpret_cast<ulonglong2 *>(smem + (uint32_t)agile::stage_bytes(T, MODE)) +
+                      (threadIdx.x >> 5) * kQueue;
+    uint32_t qn = 0;                   // queued (warp-uniform)
 
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
     const size_t ngroups = n / 8;
     const uint32_t lane = threadIdx.x & 31;
     LaneLog ll;                        // pass-2 violations: count and smallest record
+    // Full rule for access i = (a, w), noting a violation (with its range id).
+    auto decide_at = [&](size_t i, uint64_t a, uint32_t w) {
+        uint32_t rid;
+        const uint32_t v = full_rule<C32>(V, a, w, &rid);
+        if (v != AGILE_ALLOW) {
+            ll.note(i, agile::pack_info(0, v, w, rid), a);
+            verdict[i] = (uint8_t)v;
+        }
+    };
     uint32_t cnt1 = 0;                 // pass-1 denials
     size_t first1 = ~(size_t)0;        // this lane's first pass-1 denial (its smallest)
 
@@ -236,19 +279,47 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             }
             const uint32_t omask = __shfl_sync(agile::kFull, open, own & 31);
             const uint32_t oexcl = __shfl_sync(agile::kFull, excl, own & 31);
-            if (q < total) {
+            if constexpr (kDesc) {
+                size_t i = 0;
+                uint64_t a = 0;
+                uint32_t w = 0;
+                bool und = false;
+                if (q < total) {
+                    // bit 4k + h: the owner's (q - oexcl + 1)-th open access
+                    const int b = (int)__fns(omask, 0, (int)(q - oexcl) + 1);
+                    i = (g0 + 32 * (b & 3) + own) * 8 + (b >> 2);
+                    a = addr[i];
+                    w = width[i];
+                    uint32_t v;
+                    und = !desc_decide(V, a, w, &v);
+                    if (!und && v != AGILE_ALLOW) {     // range id filled in at the end
+                        ll.note(i, agile::pack_info(0, v, w, agile::kNoRange), a);
+                        verdict[i] = (uint8_t)v;
+                    }
+                }
+                const uint32_t um = __ballot_sync(agile::kFull, und);
+                if (und) s_q[qn + __popc(um & ((1u << lane) - 1u))] = make_ulonglong2(i | (uint64_t)w << 56, a);
+                qn += __popc(um);
+                if (qn >= 32) {                        // a full round of the full rule
+                    __syncwarp();
+                    const ulonglong2 e = s_q[qn - 32 + lane];
+                    decide_at(e.x & kIndexMask, e.y, (uint32_t)(e.x >> 56));
+                    qn -= 32;
+                    __syncwarp();                      // read before the slots are reused
+                }
+            } else if (q < total) {
                 // bit 4k + h: the owner's (q - oexcl + 1)-th open access
                 const int b = (int)__fns(omask, 0, (int)(q - oexcl) + 1);
                 const size_t i = (g0 + 32 * (b & 3) + own) * 8 + (b >> 2);
-                const uint64_t a = addr[i];
-                const uint32_t w = width[i];
-                uint32_t rid;
-                const uint32_t v = full_rule<C32>(V, a, w, &rid);
-                if (v != AGILE_ALLOW) {
-                    ll.note(i, agile::pack_info(0, v, w, rid), a);
-                    verdict[i] = (uint8_t)v;
-                }
+                decide_at(i, addr[i], width[i]);
             }
+        }
+    }
+    if (kDesc && qn > 0) {                             // what is left in the queue
+        __syncwarp();
+        if (lane < qn) {
+            const ulonglong2 e = s_q[lane];
+            decide_at(e.x & kIndexMask, e.y, (uint32_t)(e.x >> 56));
         }
     }
     if (blockIdx.x == 0 && threadIdx.x < 32) {        // the last n % 8 accesses
@@ -262,14 +333,16 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             verdict[i] = (uint8_t)v;
         }
     }
-    // The record of this lane's first pass-1 denial: its range id comes from the full rule.
-    if (first1 != ~(size_t)0) {
-        const uint64_t a = addr[first1];
-        const uint32_t w = width[first1];
+    // The record of this lane's first violation, from the full rule: pass 1 and the
+    // descriptors decide verdicts without range ids.
+    const size_t first = kDesc && ll.cnt != 0 && ll.key < first1 ? (size_t)ll.key : first1;
+    if (first != ~(size_t)0) {
+        const uint64_t a = addr[first];
+        const uint32_t w = width[first];
         uint32_t rid;
         const uint32_t v = full_rule<C32>(V, a, w, &rid);
-        if (ll.cnt == 0 || first1 < ll.key) {
-            ll.key = first1;
+        if (kDesc || ll.cnt == 0 || first < ll.key) {
+            ll.key = first;
             ll.info = agile::pack_info(0, v, w, rid);
             ll.addr = a;
         }
@@ -320,30 +393,43 @@ int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size
     const size_t cap = (size_t)agile::sm_count();
     const unsigned blocks = (unsigned)(want < 1 ? 1 : want > cap ? cap : want);
     if (!vec) {                                        // the class map serves pass 1 only
-        constexpr int kM = MODE & ~agile::ST_CMAP;
+        constexpr int kM = MODE & ~(agile::ST_CMAP | agile::ST_CDESC);
         return launch_kernel(k_check_batch_scalar<kM, C32>, T, a, w, n, v, log, st,
                              (uint32_t)agile::stage_bytes(T, kM), blocks);
     }
-    const uint32_t smem = (uint32_t)agile::stage_bytes(T, MODE);
+    const uint32_t smem = (uint32_t)agile::stage_bytes(T, MODE) + (MODE & agile::ST_CDESC ? kQueueBytes : 0);
     // Four (else two) groups per lane per round when the batch gives every lane that many:
-    // pass 2 then deals out more open accesses per round and its rounds run fuller.
-    if (units >= 4 * (size_t)blocks * kThreads)
+    // pass 2 then deals out more open accesses per round and its rounds run fuller. The
+    // descriptor form is launched only for such batches.
+    if constexpr ((MODE & agile::ST_CDESC) != 0) {
         return launch_kernel(k_check_batch<MODE, C32, 4>, T, a, w, n, v, log, st, smem, blocks);
-    if (units >= 2 * (size_t)blocks * kThreads)
-        return launch_kernel(k_check_batch<MODE, C32, 2>, T, a, w, n, v, log, st, smem, blocks);
-    return launch_kernel(k_check_batch<MODE, C32, 1>, T, a, w, n, v, log, st, smem, blocks);
+    } else {
+        if (units >= 4 * (size_t)blocks * kThreads)
+            return launch_kernel(k_check_batch<MODE, C32, 4>, T, a, w, n, v, log, st, smem, blocks);
+        if (units >= 2 * (size_t)blocks * kThreads)
+            return launch_kernel(k_check_batch<MODE, C32, 2>, T, a, w, n, v, log, st, smem, blocks);
+        return launch_kernel(k_check_batch<MODE, C32, 1>, T, a, w, n, v, log, st, smem, blocks);
+    }
 }
 
 // Staging: the class map always (at most 128 KiB + 4 bytes); beside it, whatever fits the
 // budget of the page map and the packed records (windows under 4 GiB) or the range
-// arrays, in that order of preference. Sections left out are read through L1.
+// arrays, in that order of preference, and the open-block descriptors with the pass-2
+// queue where they help. Sections left out are read through L1.
 template <bool C32>
 int launch_staged(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
                   uint8_t *v, LogDev *log, cudaStream_t st, bool vec) {
     using namespace agile;
     constexpr int kMPC = ST_CMAP | ST_PAGES | ST_COMPACT, kMC = ST_CMAP | ST_COMPACT;
+    constexpr int kMPCD = kMPC | ST_CDESC;
     constexpr int kMA = ST_CMAP | STAGE_ALL, kMP = ST_CMAP | ST_PAGES;
     if (T.npages == 0) return launch<STAGE_NONE, false>(T, a, w, n, v, log, st, vec);
+    // Descriptors pay off where every warp runs many rounds: a batch that gives every
+    // lane four groups or more. In a shorter one the queue's last, partly filled round of
+    // the full rule comes on top of the descriptor rounds.
+    const bool many = vec && n / 8 >= 4ull * (uint64_t)sm_count() * kThreads && n < (1ull << 56);
+    if (C32 && many && T.cdesc != nullptr && stage_bytes(T, kMPCD) + kQueueBytes <= kStageBudget)
+        return launch<kMPCD, C32>(T, a, w, n, v, log, st, vec);
     if (C32 && stage_bytes(T, kMPC) <= kStageBudget) return launch<kMPC, C32>(T, a, w, n, v, log, st, vec);
     if (C32 && stage_bytes(T, kMC) <= kStageBudget) return launch<kMC, C32>(T, a, w, n, v, log, st, vec);
     if (stage_bytes(T, kMA) <= kStageBudget) return launch<kMA, C32>(T, a, w, n, v, log, st, vec);

@@ -91,6 +91,8 @@ struct TView {
     uint32_t ulg, un;           // block size 2^ulg, blocks in the window
     const uint32_t *cmap;       // block class map (2 bits per block, cn + 1 blocks)
     uint32_t clg, cn;           // block size 2^clg, blocks in the window
+    const uint2 *cdesc;         // open-block descriptors {block, payload}, 2^dlg slots, or NULL
+    uint32_t dlg, dk1, dk2;     // their slot count (log2) and hash multipliers
 };
 
 __device__ __forceinline__ TView view_of(const agile_dev_table_t &T) {
@@ -98,7 +100,8 @@ __device__ __forceinline__ TView view_of(const agile_dev_table_t &T) {
     return TView{T.lo, T.npages, G - 1, T.lo + (T.npages << T.log2_page) - 1, T.log2_page, T.n,
                  T.search_steps, T.page, T.base, T.end, T.kind, T.id,
                  reinterpret_cast<const uint4 *>(T.crange), T.ubits, T.ubits_log2, T.ubits_n,
-                 T.cmap, T.cmap_log2, T.cmap_n};
+                 T.cmap, T.cmap_log2, T.cmap_n, reinterpret_cast<const uint2 *>(T.cdesc),
+                 T.cdesc_log2, T.cdesc_k1, T.cdesc_k2};
 }
 
 __device__ __forceinline__ uint32_t deny_of_kind(uint32_t kind) {
@@ -339,9 +342,9 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
 }
 
 // Shared-memory staging, chosen by the host as a set of sections: the page map, the
-// range arrays, the packed records, the all-user bitmap, the block class map. Laid out
-// in that order.
-enum : int { ST_PAGES = 1, ST_RANGES = 2, ST_COMPACT = 4, ST_BITS = 8, ST_CMAP = 16 };
+// range arrays, the packed records, the all-user bitmap, the block class map, the
+// open-block descriptors. Laid out in that order.
+enum : int { ST_PAGES = 1, ST_RANGES = 2, ST_COMPACT = 4, ST_BITS = 8, ST_CMAP = 16, ST_CDESC = 32 };
 enum : int {
     STAGE_NONE = 0, STAGE_PAGES = ST_PAGES, STAGE_ALL = ST_PAGES | ST_RANGES,
     STAGE_COMPACT = ST_PAGES | ST_COMPACT, STAGE_BITS = ST_BITS
@@ -357,6 +360,10 @@ __host__ __device__ inline uint32_t cmap_bytes(const agile_dev_table_t &T) {
     return round16(((uint64_t)T.cmap_n + 1 + 15) / 16 * 4);
 }
 
+__host__ __device__ inline uint32_t cdesc_bytes(const agile_dev_table_t &T) {
+    return T.cdesc != nullptr ? 8u << T.cdesc_log2 : 0u;
+}
+
 // Bytes of shared memory a staging mode needs for table T (saturating: a map too large
 // for shared memory reports more than any budget).
 __host__ __device__ inline uint64_t stage_bytes(const agile_dev_table_t &T, int mode) {
@@ -366,6 +373,7 @@ __host__ __device__ inline uint64_t stage_bytes(const agile_dev_table_t &T, int 
     if (mode & ST_COMPACT) b += round16(T.n * 16ull);       // packed records
     if (mode & ST_BITS) b += ubits_bytes(T);
     if (mode & ST_CMAP) b += cmap_bytes(T);
+    if (mode & ST_CDESC) b += cdesc_bytes(T);
     return b;
 }
 
@@ -389,12 +397,14 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     if constexpr (MODE == STAGE_NONE) return V;
     constexpr bool kPages = MODE & ST_PAGES, kRanges = MODE & ST_RANGES;
     constexpr bool kCompact = MODE & ST_COMPACT, kBits = MODE & ST_BITS, kCmap = MODE & ST_CMAP;
+    constexpr bool kDesc = MODE & ST_CDESC;
     const uint32_t pb = kPages ? round16((T.npages + 1) * 4) : 0;
     const uint32_t bb = round16(T.n * 8ull), kb = round16(T.n * 4ull);
     const uint32_t rb = kRanges ? 2 * bb + 2 * kb : 0;
     const uint32_t cb = kCompact ? round16(T.n * 16ull) : 0;
     const uint32_t ub = kBits ? ubits_bytes(T) : 0;
     const uint32_t mb = kCmap ? cmap_bytes(T) : 0;
+    const uint32_t db = kDesc ? cdesc_bytes(T) : 0;
     uint32_t *s_page = reinterpret_cast<uint32_t *>(smem);
     uint64_t *s_base = reinterpret_cast<uint64_t *>(smem + pb);
     uint64_t *s_end = reinterpret_cast<uint64_t *>(smem + pb + bb);
@@ -403,6 +413,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     uint4 *s_cr = reinterpret_cast<uint4 *>(smem + pb + rb);
     uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + pb + rb + cb);
     uint32_t *s_cmap = reinterpret_cast<uint32_t *>(smem + pb + rb + cb + ub);
+    uint2 *s_desc = reinterpret_cast<uint2 *>(smem + pb + rb + cb + ub + mb);
     const uint32_t bar = smem_addr(s_bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -410,7 +421,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t total = pb + (T.n > 0 ? rb + cb : 0) + ub + mb;
+        const uint32_t total = pb + (T.n > 0 ? rb + cb : 0) + ub + mb + db;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total)
                      : "memory");
         if (kPages) bulk_g2s(s_page, T.page, pb, bar);
@@ -423,6 +434,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
         if (kCompact && T.n > 0) bulk_g2s(s_cr, T.crange, cb, bar);
         if (kBits) bulk_g2s(s_bits, T.ubits, ub, bar);
         if (kCmap) bulk_g2s(s_cmap, T.cmap, mb, bar);
+        if (kDesc && db) bulk_g2s(s_desc, T.cdesc, db, bar);
     }
     if (!mbar_wait(bar, 0)) {               // (block-uniform only by timing: any thread may)
         if (log != nullptr && threadIdx.x == 0) atomicOr(&log->status, AGILE_LOG_STATUS_TIMEOUT);
@@ -440,6 +452,9 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
             for (uint32_t i = threadIdx.x; i < ub / 4; i += blockDim.x) s_bits[i] = T.ubits[i];
         if (kCmap)
             for (uint32_t i = threadIdx.x; i < mb / 4; i += blockDim.x) s_cmap[i] = T.cmap[i];
+        if (kDesc)
+            for (uint32_t i = threadIdx.x; i < db / 8; i += blockDim.x)
+                s_desc[i] = reinterpret_cast<const uint2 *>(T.cdesc)[i];
     }
     __syncthreads();
     if constexpr (kPages) V.page = s_page;
@@ -449,6 +464,7 @@ __device__ inline TView stage_table(const agile_dev_table_t &T, unsigned char *s
     if constexpr (kCompact) V.crange = s_cr;
     if constexpr (kBits) V.ubits = s_bits;
     if constexpr (kCmap) V.cmap = s_cmap;
+    if constexpr (kDesc) V.cdesc = s_desc;
     return V;
 }
 

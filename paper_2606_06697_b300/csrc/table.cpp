@@ -87,6 +87,97 @@ void build_cmap(const agile_guard_table &t, uint32_t *map, uint64_t window) {
     if (window != 0 && t.lo + window == 0 && nb > 0) set(nb - 1, 0);  // window ends at 2^64
 }
 
+// Descriptors of open blocks for the batch check's second pass (windows under 4 GiB, so
+// block indices and offsets are 32-bit). An open block (class 0) holding at most one
+// range boundary strictly inside it -- or none, inside one MMIO range -- is described by
+// that boundary's offset b in the block (C when there is none) and three verdicts of the
+// rule: for an access wholly before b, wholly at or after b, and across b (it overlaps
+// both regions; the rule's order MMIO, protected, user gives MMIO, PROTECTED, STRADDLE).
+// Payload: b in bits 0-13, the three verdicts in bits 16-18, 20-22, 24-26. The block
+// that ends at 2^64 is left out: an access ending there is INVALID.
+struct Desc { uint32_t block, payload; };
+
+uint32_t region_verdict(const agile_guard_table &t, uint64_t a) {   // the range holding byte a
+    const size_t j = std::upper_bound(t.base.begin(), t.base.end(), a) - t.base.begin();
+    if (j == 0 || t.end[j - 1] <= a) return AGILE_DENY_UNMAPPED;
+    const uint32_t k = t.kind[j - 1];
+    return k == AGILE_USER ? AGILE_ALLOW : k == AGILE_PROTECTED ? AGILE_DENY_PROTECTED : AGILE_DENY_MMIO;
+}
+
+uint32_t across_verdict(uint32_t vl, uint32_t vr) {
+    if (vl == AGILE_DENY_MMIO || vr == AGILE_DENY_MMIO) return AGILE_DENY_MMIO;
+    if (vl == AGILE_DENY_PROTECTED || vr == AGILE_DENY_PROTECTED) return AGILE_DENY_PROTECTED;
+    if (vl == AGILE_ALLOW || vr == AGILE_ALLOW) return AGILE_DENY_STRADDLE;
+    return AGILE_DENY_UNMAPPED;
+}
+
+std::vector<Desc> open_block_descs(const agile_guard_table &t, const uint32_t *map, uint64_t window) {
+    std::vector<Desc> out;
+    const uint64_t C = 1ull << t.cmap_log2;
+    for (uint64_t k = 0; k < t.cmap_n; ++k) {
+        if ((map[k >> 4] >> (2 * (k & 15)) & 3u) != 0) continue;
+        const uint64_t s = t.lo + k * C;               // block [s, s + C)
+        if (s + C == 0 || (k + 1 == t.cmap_n && t.lo + window == 0)) continue;
+        // distinct range edges strictly inside the block
+        uint64_t pts[3];
+        int np = 0;
+        for (const std::vector<uint64_t> *edges : {&t.base, &t.end}) {
+            auto it = std::upper_bound(edges->begin(), edges->end(), s);
+            for (; it != edges->end() && *it < s + C && np < 3; ++it) {
+                bool seen = false;
+                for (int q = 0; q < np; ++q) seen |= pts[q] == *it;
+                if (!seen) pts[np++] = *it;
+            }
+        }
+        if (np > 1) continue;
+        const uint64_t b = np ? pts[0] : s + C;
+        const uint32_t vl = region_verdict(t, s), vr = np ? region_verdict(t, b) : vl;
+        out.push_back({(uint32_t)k, (uint32_t)(b - s) | vl << 16 | vr << 20 | across_verdict(vl, vr) << 24});
+    }
+    return out;
+}
+
+// Two-choice hash of the descriptors: block k sits in slot h1(k) or h2(k) of 2^lg slots,
+// h(k) = (k * K mod 2^32) >> (32 - lg), empty slots hold block 0xFFFFFFFF. Slots: the
+// smallest power of two >= 4 per descriptor (a load of 1/4 or less, well inside what two
+// choices place), 64 to 4096. Descriptors that find no slot are left out (their accesses
+// reach the full rule). The multiplier pair placing the most descriptors is kept.
+void hash_descs(const std::vector<Desc> &d, uint32_t *lg_out, uint32_t *k1_out, uint32_t *k2_out,
+                std::vector<Desc> *slots_out) {
+    static const uint32_t kMul[16] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
+                                      0x165667B1u, 0xD3A2646Du, 0xFD7046C5u, 0xB55A4F09u,
+                                      0x7FEB352Du, 0x846CA68Bu, 0x2C1B3C6Du, 0x297A2D39u,
+                                      0xCC9E2D51u, 0x1B873593u, 0xE6546B65u, 0x68E31DA5u};
+    uint32_t lg = 6;
+    while (lg < 12 && (1ull << lg) < 4 * d.size()) ++lg;
+    const uint32_t S = 1u << lg;
+    size_t best = 0;
+    for (int t = 0; t < 8; ++t) {
+        const uint32_t k1 = kMul[2 * t], k2 = kMul[2 * t + 1];
+        auto h = [&](uint32_t k, uint32_t K) { return (uint32_t)(k * K) >> (32 - lg); };
+        std::vector<Desc> slot(S, Desc{0xFFFFFFFFu, 0});
+        size_t placed = 0;
+        for (const Desc &x : d) {
+            Desc cur = x;
+            uint32_t pos = h(cur.block, k1);
+            bool ok = false;
+            for (int kick = 0; kick < 64; ++kick) {
+                if (slot[pos].block == 0xFFFFFFFFu) { slot[pos] = cur; ok = true; break; }
+                std::swap(cur, slot[pos]);
+                const uint32_t a1 = h(cur.block, k1);
+                pos = pos == a1 ? h(cur.block, k2) : a1;
+            }
+            placed += ok;                              // else `cur`, whichever it is, is left out
+        }
+        if (t == 0 || placed > best) {
+            best = placed;
+            *lg_out = lg; *k1_out = k1; *k2_out = k2;
+            *slots_out = slot;
+        }
+        if (placed == d.size()) break;
+    }
+}
+
 // Page size for AGILE_PAGE_AUTO: the largest page, from 2 MiB down to 4 KiB, at which at
 // least 95% of the user bytes lie in pages that are all one user range (the accesses the
 // page map decides alone), keeping the map within 2^24 entries; failing that, the page
@@ -214,6 +305,15 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
         t->cmap_n = (uint32_t)((window >> clg) + ((window & ((1ull << clg) - 1)) != 0));
         t->off_cmap = off;
         off += align256(((uint64_t)t->cmap_n + 1 + 15) / 16 * 4);
+        std::vector<uint32_t> cmap_img(((uint64_t)t->cmap_n + 1 + 15) / 16, 0);
+        build_cmap(*t, cmap_img.data(), window);
+        std::vector<Desc> slots;
+        if (t->compact) {
+            hash_descs(open_block_descs(*t, cmap_img.data(), window), &t->cdesc_log2, &t->cdesc_k1,
+                       &t->cdesc_k2, &slots);
+            t->off_cdesc = off;
+            off += align256(slots.size() * 8);
+        }
         t->total = off;
         t->staging.assign(t->total, 0);
         {
@@ -227,7 +327,8 @@ int agile_guard_table_build(const agile_range_t *h_ranges, size_t n, uint32_t lo
                 for (; k < k_end; ++k) ub[k >> 5] |= 1u << (k & 31);
             }
         }
-        build_cmap(*t, reinterpret_cast<uint32_t *>(t->staging.data() + t->off_cmap), window);
+        std::memcpy(t->staging.data() + t->off_cmap, cmap_img.data(), cmap_img.size() * 4);
+        if (t->compact) std::memcpy(t->staging.data() + t->off_cdesc, slots.data(), slots.size() * 8);
         std::memcpy(t->staging.data() + kTablePageOff, t->page.data(), t->page.size() * 4);
         if (n) {
             std::memcpy(t->staging.data() + t->off_base, t->base.data(), n * 8);
@@ -303,6 +404,12 @@ int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, 
     h.cmap = (const uint32_t *)(d + t->off_cmap);
     h.cmap_log2 = t->cmap_log2;
     h.cmap_n = t->cmap_n;
+    if (t->compact) {
+        h.cdesc = (const uint32_t *)(d + t->off_cdesc);
+        h.cdesc_log2 = t->cdesc_log2;
+        h.cdesc_k1 = t->cdesc_k1;
+        h.cdesc_k2 = t->cdesc_k2;
+    }
     static_assert(sizeof(agile_dev_table_t) <= kTableHeaderBytes, "header fits");
     std::memcpy(t->staging.data(), &h, sizeof h);
     std::memset(t->staging.data() + kTableZeroOff, 0, 128);
