@@ -268,9 +268,10 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
         }
         const uint32_t total = __shfl_sync(agile::kFull, incl, 31);
         const uint32_t excl = incl - c;
-        __syncwarp();                                  // the pass-1 stores above come first
-        for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-            const uint32_t q = q0 + lane;
+        // Index of the warp's q-th open access (q < total), called by all lanes: its owner
+        // is the first lane whose inclusive count exceeds q, and it is bit 4k + h of the
+        // owner's mask, the (q - owner's exclusive count + 1)-th bit set there.
+        auto dealt = [&](uint32_t q) -> size_t {
             uint32_t own = 0;                          // lanes whose open accesses all precede q
 #pragma unroll
             for (int step = 16; step; step >>= 1) {
@@ -279,39 +280,57 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             }
             const uint32_t omask = __shfl_sync(agile::kFull, open, own & 31);
             const uint32_t oexcl = __shfl_sync(agile::kFull, excl, own & 31);
-            if constexpr (kDesc) {
-                size_t i = 0;
-                uint64_t a = 0;
-                uint32_t w = 0;
-                bool und = false;
-                if (q < total) {
-                    // bit 4k + h: the owner's (q - oexcl + 1)-th open access
-                    const int b = (int)__fns(omask, 0, (int)(q - oexcl) + 1);
-                    i = (g0 + 32 * (b & 3) + own) * 8 + (b >> 2);
-                    a = addr[i];
-                    w = width[i];
-                    uint32_t v;
-                    und = !desc_decide(V, a, w, &v);
-                    if (!und && v != AGILE_ALLOW) {     // range id filled in at the end
-                        ll.note(i, agile::pack_info(0, v, w, agile::kNoRange), a);
-                        verdict[i] = (uint8_t)v;
+            const int b = (int)__fns(omask, 0, (int)(q - oexcl) + 1);
+            return (g0 + 32 * (b & 3) + own) * 8 + (b >> 2);
+        };
+        __syncwarp();                                  // the pass-1 stores above come first
+        if constexpr (kDesc) {
+            // Two rounds at a time: both rounds' inputs are loaded before either is decided.
+            for (uint32_t q0 = 0; q0 < total; q0 += 64) {
+                size_t ir[2] = {0, 0};
+                uint64_t ar[2] = {0, 0};
+                uint32_t wr[2] = {0, 0};
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const uint32_t q = q0 + 32 * r + lane;
+                    if (r == 1 && q0 + 32 >= total) break;          // warp-uniform
+                    const size_t i = dealt(q);
+                    if (q < total) {
+                        ir[r] = i;
+                        ar[r] = addr[i];
+                        wr[r] = width[i];
                     }
                 }
-                const uint32_t um = __ballot_sync(agile::kFull, und);
-                if (und) s_q[qn + __popc(um & ((1u << lane) - 1u))] = make_ulonglong2(i | (uint64_t)w << 56, a);
-                qn += __popc(um);
-                if (qn >= 32) {                        // a full round of the full rule
-                    __syncwarp();
-                    const ulonglong2 e = s_q[qn - 32 + lane];
-                    decide_at(e.x & kIndexMask, e.y, (uint32_t)(e.x >> 56));
-                    qn -= 32;
-                    __syncwarp();                      // read before the slots are reused
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    bool und = false;
+                    if (q0 + 32 * r + lane < total) {
+                        uint32_t v;
+                        und = !desc_decide(V, ar[r], wr[r], &v);
+                        if (!und && v != AGILE_ALLOW) {    // range id filled in at the end
+                            ll.note(ir[r], agile::pack_info(0, v, wr[r], agile::kNoRange), ar[r]);
+                            verdict[ir[r]] = (uint8_t)v;
+                        }
+                    }
+                    const uint32_t um = __ballot_sync(agile::kFull, und);
+                    if (und)
+                        s_q[qn + __popc(um & ((1u << lane) - 1u))] =
+                            make_ulonglong2(ir[r] | (uint64_t)wr[r] << 56, ar[r]);
+                    qn += __popc(um);
+                    if (qn >= 32) {                    // a full round of the full rule
+                        __syncwarp();
+                        const ulonglong2 e = s_q[qn - 32 + lane];
+                        decide_at(e.x & kIndexMask, e.y, (uint32_t)(e.x >> 56));
+                        qn -= 32;
+                        __syncwarp();                  // read before the slots are reused
+                    }
                 }
-            } else if (q < total) {
-                // bit 4k + h: the owner's (q - oexcl + 1)-th open access
-                const int b = (int)__fns(omask, 0, (int)(q - oexcl) + 1);
-                const size_t i = (g0 + 32 * (b & 3) + own) * 8 + (b >> 2);
-                decide_at(i, addr[i], width[i]);
+            }
+        } else {
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const size_t i = dealt(q);
+                if (q < total) decide_at(i, addr[i], width[i]);
             }
         }
     }

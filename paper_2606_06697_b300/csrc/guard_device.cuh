@@ -240,21 +240,31 @@ __device__ __forceinline__ void cas128(unsigned long long *p, unsigned long long
         : "memory");
 }
 
-// Lower the 128-bit word at p to (k, v) if that is lexicographically smaller. Each failed
-// exchange sees a strictly smaller word, so the loop ends; the bound is a backstop.
-__device__ inline void cas_min128(unsigned long long *p, unsigned long long k,
-                                  unsigned long long v, uint32_t *status) {
-    unsigned long long ok = *(volatile unsigned long long *)p;
-    unsigned long long ov = *(volatile unsigned long long *)(p + 1);
+// Lower the log's two first-record words, (key, info) and (key, addr), to the block's
+// (k, v) and (k, a) where those are smaller. Both words are read at once and both
+// exchanges are issued before either result is awaited, so a block ending its kernel
+// waits two round trips to L2, not four. Each failed exchange sees a strictly smaller
+// word, so the loop ends; the bound is a backstop.
+__device__ inline void log_min_first(LogDev *L, unsigned long long k, unsigned long long v,
+                                     unsigned long long a) {
+    unsigned long long fk, fv, wk, wa;
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(fk), "=l"(fv) : "l"(&L->first_key));
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(wk), "=l"(wa) : "l"(&L->where_key));
     for (int it = 0; it < (1 << 16); ++it) {
-        if (!(k < ok || (k == ok && v < ov))) return;
-        unsigned long long rk, rv;
-        cas128(p, ok, ov, k, v, rk, rv);
-        if (rk == ok && rv == ov) return;
-        ok = rk;
-        ov = rv;
+        const bool df = k < fk || (k == fk && v < fv);
+        const bool dw = k < wk || (k == wk && a < wa);
+        if (!df && !dw) return;
+        unsigned long long rfk = fk, rfv = fv, rwk = wk, rwa = wa;
+        if (df) cas128(&L->first_key, fk, fv, k, v, rfk, rfv);
+        if (dw) cas128(&L->where_key, wk, wa, k, a, rwk, rwa);
+        // a word that took ours now holds ours; one that did not holds what the exchange saw
+        const bool okf = df && rfk == fk && rfv == fv, okw = dw && rwk == wk && rwa == wa;
+        fk = okf ? k : rfk;
+        fv = okf ? v : rfv;
+        wk = okw ? k : rwk;
+        wa = okw ? a : rwa;
     }
-    atomicOr(status, AGILE_LOG_STATUS_TIMEOUT);
+    atomicOr(&L->status, AGILE_LOG_STATUS_TIMEOUT);
 }
 
 // Per-thread running minimum of the violations it has seen; each is also appended to the
@@ -305,8 +315,7 @@ __device__ inline void block_log_flush(LogDev *L, const LaneLog &ll) {
         for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
         if (lane == 0 && total != 0 && L != nullptr) {
             atomicAdd(&L->count, total);
-            cas_min128(&L->first_key, k, v, &L->status);
-            cas_min128(&L->where_key, k, a, &L->status);
+            log_min_first(L, k, v, a);
         }
     }
 }
@@ -512,8 +521,7 @@ __device__ inline void slots_flush(LogDev *L, WarpSlots &S) {
         for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
         if (lane == 0 && total != 0 && L != nullptr) {
             atomicAdd(&L->count, total);
-            cas_min128(&L->first_key, k, v, &L->status);
-            cas_min128(&L->where_key, k, a, &L->status);
+            log_min_first(L, k, v, a);
         }
     }
 }
