@@ -352,22 +352,23 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             verdict[i] = (uint8_t)v;
         }
     }
-    // The record of this lane's first violation, from the full rule: pass 1 and the
-    // descriptors decide verdicts without range ids.
-    const size_t first = kDesc && ll.cnt != 0 && ll.key < first1 ? (size_t)ll.key : first1;
-    if (first != ~(size_t)0) {
-        const uint64_t a = addr[first];
-        const uint32_t w = width[first];
-        uint32_t rid;
-        const uint32_t v = full_rule<C32>(V, a, w, &rid);
-        if (kDesc || ll.cnt == 0 || first < ll.key) {
-            ll.key = first;
-            ll.info = agile::pack_info(0, v, w, rid);
-            ll.addr = a;
-        }
+    // Violations are keyed by index, one key per access: the block reduces them by key
+    // alone. Pass 1 and the descriptors decide verdicts without range ids, so the block's
+    // smallest record is completed from the full rule -- only when it lowers the log.
+    if (first1 != ~(size_t)0 && (ll.cnt == 0 || first1 < ll.key)) {
+        ll.key = first1;
+        ll.info = 0;
+        ll.addr = 0;
     }
     ll.cnt += cnt1;
-    agile::block_log_flush(log, ll);
+    agile::block_log_flush(log, ll, [&](unsigned long long k, unsigned long long &info,
+                                        unsigned long long &a) {
+        a = addr[k];
+        const uint32_t w = width[k];
+        uint32_t rid;
+        const uint32_t v = full_rule<C32>(V, a, w, &rid);
+        info = agile::pack_info(0, v, w, rid);
+    });
 }
 
 // Inputs not aligned for vector loads, or a log with a bounded list: one access per

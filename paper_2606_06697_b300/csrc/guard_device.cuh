@@ -240,20 +240,35 @@ __device__ __forceinline__ void cas128(unsigned long long *p, unsigned long long
         : "memory");
 }
 
+// Completion of a block's smallest record before it goes into the log: none for kernels
+// that note whole records.
+struct RecordWhole {
+    __device__ void operator()(unsigned long long, unsigned long long &, unsigned long long &) const {}
+};
+
 // Lower the log's two first-record words, (key, info) and (key, addr), to the block's
 // (k, v) and (k, a) where those are smaller. Both words are read at once and both
 // exchanges are issued before either result is awaited, so a block ending its kernel
-// waits two round trips to L2, not four. Each failed exchange sees a strictly smaller
-// word, so the loop ends; the bound is a backstop.
+// waits two round trips to L2, not four. A kernel that keys its violations uniquely may
+// reduce them by key alone and leave (v, a) to `complete`, which runs only once the
+// record is known to lower the log. Each failed exchange sees a strictly smaller word,
+// so the loop ends; the bound is a backstop.
+template <typename Complete = RecordWhole>
 __device__ inline void log_min_first(LogDev *L, unsigned long long k, unsigned long long v,
-                                     unsigned long long a) {
+                                     unsigned long long a, Complete complete = Complete()) {
     unsigned long long fk, fv, wk, wa;
     asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(fk), "=l"(fv) : "l"(&L->first_key));
     asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(wk), "=l"(wa) : "l"(&L->where_key));
+    bool whole = false;
     for (int it = 0; it < (1 << 16); ++it) {
         const bool df = k < fk || (k == fk && v < fv);
         const bool dw = k < wk || (k == wk && a < wa);
         if (!df && !dw) return;
+        if (!whole) {                  // compare again with the completed record
+            complete(k, v, a);
+            whole = true;
+            continue;
+        }
         unsigned long long rfk = fk, rfv = fv, rwk = wk, rwa = wa;
         if (df) cas128(&L->first_key, fk, fv, k, v, rfk, rfv);
         if (dw) cas128(&L->where_key, wk, wa, k, a, rwk, rwa);
@@ -294,8 +309,10 @@ __device__ __forceinline__ void min3_shfl(unsigned long long &k, unsigned long l
 
 // Block-collective, called once by every thread at the end of a kernel: the block's
 // violations are reduced to one count and one smallest record in shared memory, and one
-// thread updates the log. One global update per block keeps the log address cold.
-__device__ inline void block_log_flush(LogDev *L, const LaneLog &ll) {
+// thread updates the log (completing the record first, see log_min_first). One global
+// update per block keeps the log address cold.
+template <typename Complete = RecordWhole>
+__device__ inline void block_log_flush(LogDev *L, const LaneLog &ll, Complete complete = Complete()) {
     __shared__ unsigned long long s_key[32], s_info[32], s_addr[32];
     __shared__ uint32_t s_cnt[32];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -315,7 +332,7 @@ __device__ inline void block_log_flush(LogDev *L, const LaneLog &ll) {
         for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
         if (lane == 0 && total != 0 && L != nullptr) {
             atomicAdd(&L->count, total);
-            log_min_first(L, k, v, a);
+            log_min_first(L, k, v, a, complete);
         }
     }
 }
