@@ -247,39 +247,37 @@ struct RecordWhole {
 };
 
 // Lower the log's two first-record words, (key, info) and (key, addr), to the block's
-// (k, v) and (k, a) where those are smaller. Both words are read at once and both
-// exchanges are issued before either result is awaited, so a block ending its kernel
-// waits two round trips to L2, not four. A kernel that keys its violations uniquely may
-// reduce them by key alone and leave (v, a) to `complete`, which runs only once the
-// record is known to lower the log. Each failed exchange sees a strictly smaller word,
-// so the loop ends; the bound is a backstop.
+// (k, v) and (k, a) where those are smaller. Blocks of one launch end at nearly the same
+// time, so their updates meet on one L2 line. Each block first lowers where_key alone
+// with a 64-bit atomic minimum, which that line takes at the L2's atomic rate; a block
+// whose key is above the value it gets back has lost and stops. Only the few that lowered
+// it (or tied) complete their record -- a kernel that keys its violations uniquely may
+// reduce them by key alone and leave (v, a) to `complete` -- and take the 128-bit
+// exchanges: the (key, info) word by lexicographic minimum, and the address beside
+// where_key while where_key still holds their key (a smaller key's block writes its own).
+// Each failed exchange sees a different word, and the loops are bounded as a backstop.
 template <typename Complete = RecordWhole>
 __device__ inline void log_min_first(LogDev *L, unsigned long long k, unsigned long long v,
                                      unsigned long long a, Complete complete = Complete()) {
-    unsigned long long fk, fv, wk, wa;
-    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(fk), "=l"(fv) : "l"(&L->first_key));
-    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(wk), "=l"(wa) : "l"(&L->where_key));
-    bool whole = false;
-    for (int it = 0; it < (1 << 16); ++it) {
-        const bool df = k < fk || (k == fk && v < fv);
-        const bool dw = k < wk || (k == wk && a < wa);
-        if (!df && !dw) return;
-        if (!whole) {                  // compare again with the completed record
-            complete(k, v, a);
-            whole = true;
-            continue;
-        }
-        unsigned long long rfk = fk, rfv = fv, rwk = wk, rwa = wa;
-        if (df) cas128(&L->first_key, fk, fv, k, v, rfk, rfv);
-        if (dw) cas128(&L->where_key, wk, wa, k, a, rwk, rwa);
-        // a word that took ours now holds ours; one that did not holds what the exchange saw
-        const bool okf = df && rfk == fk && rfv == fv, okw = dw && rwk == wk && rwa == wa;
-        fk = okf ? k : rfk;
-        fv = okf ? v : rfv;
-        wk = okw ? k : rwk;
-        wa = okw ? a : rwa;
+    if (k > atomicMin(&L->where_key, k)) return;
+    complete(k, v, a);
+    unsigned long long fk = ~0ull, fv = ~0ull;         // first guess: an empty log
+    int it = 0;
+    for (; it < (1 << 16) && (k < fk || (k == fk && v < fv)); ++it) {
+        unsigned long long rk, rv;
+        cas128(&L->first_key, fk, fv, k, v, rk, rv);
+        if (rk == fk && rv == fv) break;
+        fk = rk;
+        fv = rv;
     }
-    atomicOr(&L->status, AGILE_LOG_STATUS_TIMEOUT);
+    unsigned long long wa = ~0ull;
+    for (; it < (1 << 16); ++it) {
+        unsigned long long rk, ra;
+        cas128(&L->where_key, k, wa, k, a, rk, ra);
+        if (rk != k || ra == wa || ra == a) break;    // a smaller key came, or ours is in
+        wa = ra;
+    }
+    if (it >= (1 << 16)) atomicOr(&L->status, AGILE_LOG_STATUS_TIMEOUT);
 }
 
 // Per-thread running minimum of the violations it has seen; each is also appended to the
