@@ -434,14 +434,15 @@ int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size
 
 // Staging: the class map always (at most 128 KiB + 4 bytes); beside it, whatever fits the
 // budget of the page map and the packed records (windows under 4 GiB) or the range
-// arrays, in that order of preference, and the open-block descriptors with the pass-2
-// queue where they help. Sections left out are read through L1.
+// arrays, and the open-block descriptors with the pass-2 queue where they help, in this
+// order of preference: everything; descriptors and records without the page map; the
+// page map and records; records; ranges; pages. Sections left out are read through L1.
 template <bool C32>
 int launch_staged(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size_t n,
                   uint8_t *v, LogDev *log, cudaStream_t st, bool vec) {
     using namespace agile;
     constexpr int kMPC = ST_CMAP | ST_PAGES | ST_COMPACT, kMC = ST_CMAP | ST_COMPACT;
-    constexpr int kMPCD = kMPC | ST_CDESC;
+    constexpr int kMPCD = kMPC | ST_CDESC, kMCD = kMC | ST_CDESC;
     constexpr int kMA = ST_CMAP | STAGE_ALL, kMP = ST_CMAP | ST_PAGES;
     if (T.npages == 0) return launch<STAGE_NONE, false>(T, a, w, n, v, log, st, vec);
     // Descriptors pay off where every warp runs many rounds: a batch that gives every
@@ -450,6 +451,9 @@ int launch_staged(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *
     const bool many = vec && n / 8 >= 4ull * (uint64_t)sm_count() * kThreads && n < (1ull << 56);
     if (C32 && many && T.cdesc != nullptr && stage_bytes(T, kMPCD) + kQueueBytes <= kStageBudget)
         return launch<kMPCD, C32>(T, a, w, n, v, log, st, vec);
+    // the descriptors before the page map: they decide most open accesses without it
+    if (C32 && many && T.cdesc != nullptr && stage_bytes(T, kMCD) + kQueueBytes <= kStageBudget)
+        return launch<kMCD, C32>(T, a, w, n, v, log, st, vec);
     if (C32 && stage_bytes(T, kMPC) <= kStageBudget) return launch<kMPC, C32>(T, a, w, n, v, log, st, vec);
     if (C32 && stage_bytes(T, kMC) <= kStageBudget) return launch<kMC, C32>(T, a, w, n, v, log, st, vec);
     if (stage_bytes(T, kMA) <= kStageBudget) return launch<kMA, C32>(T, a, w, n, v, log, st, vec);

@@ -134,6 +134,27 @@ def test_batch_parity_dense_boundaries(n_ranges, seed, lg_page):
     assert_log_equal(rec, olog, client=3)
 
 
+@pytest.mark.parametrize("lg_page", [12, 16, 21])
+def test_batch_parity_workload_descriptor_form(lg_page):
+    """The batch workload repeated to the descriptor form's size: at 4 KiB and 64 KiB pages
+    the page map does not fit in shared memory beside the class map, descriptors and
+    queue, and the form without the staged page map runs."""
+    t = syn.batch_table()
+    addr, width, label = syn.batch_accesses(t, 1 << 20)
+    m = desc_batch()
+    reps = -(-m // len(addr))
+    addr, width, label = (np.tile(x, reps)[:m] for x in (addr, width, label))
+    tbl, dev = device_table(t, lg_page)
+    if lg_page == 12:
+        assert tbl.geometry()[1] * 4 > 96 * 1024          # the page map alone is 1 MiB
+    v, rc, rec = run_batch(dev, addr, width, client=4)
+    assert (v == label).all()
+    _, _, olog = oracle.check_batch(t, addr[:1 << 20], width[:1 << 20], method="sorted")
+    assert rec.count == int((label != 0).sum())
+    assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
+        (olog.key, olog.addr, olog.width, olog.verdict, olog.range_id)
+
+
 def test_batch_parity_descriptor_first_record():
     """The smallest denied index decided by a descriptor: the log's first record carries
     the range id the full rule finds."""
