@@ -146,9 +146,12 @@ __device__ __forceinline__ uint32_t cmap_code(const TView &V, uint64_t a, uint32
     return ok && legal_width(w) ? code : 0u;
 }
 
-// Pass-2 decision from the open-block descriptors (windows under 4 GiB): false when the
-// access's block has no descriptor, or the access is not inside one block of the window
-// with a legal width. Branch-free: both slots of the two-choice hash are read.
+// Pass-2 decision from the open-block descriptors (windows under 4 GiB), for an access
+// with a legal width: inside one described block, from its descriptor; wholly outside
+// the window (which spans less than 4 GiB from lo), UNMAPPED. False otherwise -- no
+// descriptor, across a block edge, reaching into the window from below, an end past
+// 2^64 - 1 -- and the full rule decides. Branch-free: both slots of the two-choice hash
+// are read.
 __device__ __forceinline__ bool desc_decide(const TView &V, uint64_t a, uint32_t w, uint32_t *v) {
     const uint64_t off = a - V.lo;
     const uint32_t o = (uint32_t)off;
@@ -160,8 +163,10 @@ __device__ __forceinline__ bool desc_decide(const TView &V, uint64_t a, uint32_t
     const uint32_t p = d1.x == k ? d1.y : d2.y;
     const uint32_t b = p & 0x3FFFu;                    // the boundary, C when none
     const uint32_t f = e <= b ? 16u : oi >= b ? 20u : 24u;   // before, at or after, across
-    *v = (p >> f) & 7u;
-    return hit && (off >> 32) == 0 && e <= (1u << V.clg) && legal_width(w);
+    const bool outside = (off >> 32) != 0;
+    const bool clear = !(a < V.lo && a + w > V.lo) && a <= ~0ull - w;
+    *v = outside ? (uint32_t)AGILE_DENY_UNMAPPED : (p >> f) & 7u;
+    return legal_width(w) && (outside ? clear : hit && e <= (1u << V.clg));
 }
 
 // Full rule for one access (pass 2, the n mod 8 tail, and the misaligned form).
@@ -185,6 +190,10 @@ __device__ __forceinline__ uint32_t full_rule(const TView &V, uint64_t a, uint32
 constexpr uint32_t kQueue = 64;
 constexpr uint32_t kQueueBytes = kThreads / 32 * kQueue * 16;
 constexpr uint64_t kIndexMask = (1ull << 56) - 1;   // indices below 2^56
+// Per-warp list of a round of groups' open accesses (lane << 5 | bit), written by their
+// owners, when they number at most kList.
+constexpr uint32_t kList = 256;
+constexpr uint32_t kListBytes = kThreads / 32 * kList * 2;
 
 template <int MODE, bool C32, int kG>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -195,9 +204,10 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     __shared__ unsigned long long s_bar;
     const TView V = agile::stage_table<MODE>(T, smem, &s_bar, log);
     constexpr bool kDesc = C32 && (MODE & agile::ST_CDESC);
-    // the queue follows the staged sections
-    ulonglong2 *s_q = reinterpret_cast<ulonglong2 *>(smem + (uint32_t)agile::stage_bytes(T, MODE)) +
-                      (threadIdx.x >> 5) * kQueue;
+    // the queue and the list follow the staged sections
+    const uint32_t staged = (uint32_t)agile::stage_bytes(T, MODE);
+    ulonglong2 *s_q = reinterpret_cast<ulonglong2 *>(smem + staged) + (threadIdx.x >> 5) * kQueue;
+    uint16_t *s_list = reinterpret_cast<uint16_t *>(smem + staged + kQueueBytes) + (threadIdx.x >> 5) * kList;
     uint32_t qn = 0;                   // queued (warp-uniform)
 
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -285,6 +295,18 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
         };
         __syncwarp();                                  // the pass-1 stores above come first
         if constexpr (kDesc) {
+            // Where they fit the warp's list, each lane writes out its own open accesses,
+            // in order from its exclusive count, and a round reads its access's position
+            // there; else the owner search deals them.
+            const bool listed = total <= kList;            // warp-uniform
+            if (listed) {
+                uint32_t m = open, pos = excl;
+                while (m != 0) {
+                    s_list[pos++] = (uint16_t)(lane << 5 | (uint32_t)(__ffs(m) - 1));
+                    m &= m - 1;
+                }
+                __syncwarp();
+            }
             // Two rounds at a time: both rounds' inputs are loaded before either is decided.
             for (uint32_t q0 = 0; q0 < total; q0 += 64) {
                 size_t ir[2] = {0, 0};
@@ -294,7 +316,15 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
                 for (int r = 0; r < 2; ++r) {
                     const uint32_t q = q0 + 32 * r + lane;
                     if (r == 1 && q0 + 32 >= total) break;          // warp-uniform
-                    const size_t i = dealt(q);
+                    size_t i = 0;
+                    if (listed) {
+                        if (q < total) {
+                            const uint32_t id = s_list[q];          // lane << 5 | (4k + h)
+                            i = (g0 + 32 * (id & 3) + (id >> 5)) * 8 + ((id >> 2) & 7);
+                        }
+                    } else {
+                        i = dealt(q);
+                    }
                     if (q < total) {
                         ir[r] = i;
                         ar[r] = addr[i];
@@ -326,6 +356,7 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
                     }
                 }
             }
+            __syncwarp();                              // the list is read before it is rewritten
         } else {
             for (uint32_t q0 = 0; q0 < total; q0 += 32) {
                 const uint32_t q = q0 + lane;
@@ -417,7 +448,7 @@ int launch(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *w, size
         return launch_kernel(k_check_batch_scalar<kM, C32>, T, a, w, n, v, log, st,
                              (uint32_t)agile::stage_bytes(T, kM), blocks);
     }
-    const uint32_t smem = (uint32_t)agile::stage_bytes(T, MODE) + (MODE & agile::ST_CDESC ? kQueueBytes : 0);
+    const uint32_t smem = (uint32_t)agile::stage_bytes(T, MODE) + (MODE & agile::ST_CDESC ? kQueueBytes + kListBytes : 0);
     // Four (else two) groups per lane per round when the batch gives every lane that many:
     // pass 2 then deals out more open accesses per round and its rounds run fuller. The
     // descriptor form is launched only for such batches.
@@ -449,10 +480,10 @@ int launch_staged(const agile_dev_table_t &T, const uint64_t *a, const uint8_t *
     // lane four groups or more. In a shorter one the queue's last, partly filled round of
     // the full rule comes on top of the descriptor rounds.
     const bool many = vec && n / 8 >= 4ull * (uint64_t)sm_count() * kThreads && n < (1ull << 56);
-    if (C32 && many && T.cdesc != nullptr && stage_bytes(T, kMPCD) + kQueueBytes <= kStageBudget)
+    if (C32 && many && T.cdesc != nullptr && stage_bytes(T, kMPCD) + kQueueBytes + kListBytes <= kStageBudget)
         return launch<kMPCD, C32>(T, a, w, n, v, log, st, vec);
     // the descriptors before the page map: they decide most open accesses without it
-    if (C32 && many && T.cdesc != nullptr && stage_bytes(T, kMCD) + kQueueBytes <= kStageBudget)
+    if (C32 && many && T.cdesc != nullptr && stage_bytes(T, kMCD) + kQueueBytes + kListBytes <= kStageBudget)
         return launch<kMCD, C32>(T, a, w, n, v, log, st, vec);
     if (C32 && stage_bytes(T, kMPC) <= kStageBudget) return launch<kMPC, C32>(T, a, w, n, v, log, st, vec);
     if (C32 && stage_bytes(T, kMC) <= kStageBudget) return launch<kMC, C32>(T, a, w, n, v, log, st, vec);
