@@ -214,13 +214,20 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
     const size_t nthreads = (size_t)gridDim.x * blockDim.x;
     const size_t ngroups = n / 8;
     const uint32_t lane = threadIdx.x & 31;
-    LaneLog ll;                        // pass-2 violations: count and smallest record
-    // Full rule for access i = (a, w), noting a violation (with its range id).
+    // Pass-2 violations: their count and smallest key (access index). The block's smallest
+    // violation gets its record from the full rule at the end (see below), so no lane keeps
+    // more than the key.
+    LaneLog ll;
+    auto note_key = [&](size_t i) {
+        ++ll.cnt;
+        ll.key = i < ll.key ? i : ll.key;
+    };
+    // Full rule for access i = (a, w), noting a violation.
     auto decide_at = [&](size_t i, uint64_t a, uint32_t w) {
         uint32_t rid;
         const uint32_t v = full_rule<C32>(V, a, w, &rid);
         if (v != AGILE_ALLOW) {
-            ll.note(i, agile::pack_info(0, v, w, rid), a);
+            note_key(i);
             verdict[i] = (uint8_t)v;
         }
     };
@@ -337,8 +344,8 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
                     if (q0 + 32 * r + lane < total) {
                         uint32_t v;
                         und = !desc_decide(V, ar[r], wr[r], &v);
-                        if (!und && v != AGILE_ALLOW) {    // range id filled in at the end
-                            ll.note(ir[r], agile::pack_info(0, v, wr[r], agile::kNoRange), ar[r]);
+                        if (!und && v != AGILE_ALLOW) {
+                            note_key(ir[r]);
                             verdict[ir[r]] = (uint8_t)v;
                         }
                     }
@@ -379,18 +386,16 @@ k_check_batch(const agile_dev_table_t T, const uint64_t *__restrict__ addr,
             const uint32_t w = width[i];
             uint32_t rid;
             const uint32_t v = full_rule<C32>(V, a, w, &rid);
-            if (v != AGILE_ALLOW) ll.note(i, agile::pack_info(0, v, w, rid), a);
+            if (v != AGILE_ALLOW) note_key(i);
             verdict[i] = (uint8_t)v;
         }
     }
     // Violations are keyed by index, one key per access: the block reduces them by key
-    // alone. Pass 1 and the descriptors decide verdicts without range ids, so the block's
-    // smallest record is completed from the full rule -- only when it lowers the log.
-    if (first1 != ~(size_t)0 && (ll.cnt == 0 || first1 < ll.key)) {
-        ll.key = first1;
-        ll.info = 0;
-        ll.addr = 0;
-    }
+    // alone, and its smallest violation's record -- verdict, width, address, range id --
+    // comes from the full rule, only once the log shows it lower.
+    if (first1 < ll.key) ll.key = first1;
+    ll.info = 0;
+    ll.addr = 0;
     ll.cnt += cnt1;
     agile::block_log_flush(log, ll, [&](unsigned long long k, unsigned long long &info,
                                         unsigned long long &a) {
