@@ -32,6 +32,28 @@ __device__ __forceinline__ bool legal_width(uint32_t w) {
     return w <= 16 && ((0x10116u >> w) & 1u);        // 1, 2, 4, 8, 16
 }
 
+// x >> s with the PTX rule for shift counts of 32 and more (the result is 0).
+__device__ __forceinline__ uint32_t shr_clamped(uint32_t x, uint32_t s) {
+    uint32_t r;
+    asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
+    return r;
+}
+
+// The verdict alone, for the vector path: a legal width (the clamped shift is 0 for
+// widths of 32 and more) and an end that does not wrap past 2^64 - 1, then the first
+// aperture the access overlaps.
+template <int N>
+__device__ __forceinline__ uint32_t verdict_of(const Apertures &A, uint64_t a, uint32_t w) {
+    const uint64_t e = a + w;
+    uint32_t v = AGILE_ALLOW;
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {                // the lowest i overlapped wins
+        const bool hit = a < A.end[i] && e > A.lo[i];
+        v = hit ? A.verdict[i] : v;
+    }
+    return (shr_clamped(0x10116u, w) & 1u) && e > a ? v : (uint32_t)AGILE_DENY_INVALID;
+}
+
 // Verdict of one access against the first N apertures (N fixed per launch, so the loop
 // unrolls to exactly the apertures there are).
 template <int N>
@@ -79,28 +101,25 @@ k_aperture_batch(const Apertures A, const uint64_t *__restrict__ addr,
                 av[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
             }
             const uint64_t wv = __ldcs(reinterpret_cast<const unsigned long long *>(width + g * 8));
-            uint64_t out = 0;
-            uint32_t rid0 = AGILE_NO_RANGE;
+            // verdict k into byte k, as multiply-adds (FMA pipe; the compares fill the ALU)
+            uint32_t vlo = 0, vhi = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                uint32_t rid;
-                const uint32_t v = decide<N>(A, av[k], (uint32_t)(wv >> (8 * k)) & 0xFFu, &rid);
-                rid0 = (out == 0 && v != AGILE_ALLOW) ? rid : rid0;   // the group's first denial
-                out |= (uint64_t)v << (8 * k);
+                const uint32_t wk = __byte_perm(k < 4 ? (uint32_t)wv : (uint32_t)(wv >> 32), 0u,
+                                                0x4440u | (uint32_t)(k & 3));
+                const uint32_t v = verdict_of<N>(A, av[k], wk);
+                if (k < 4) asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(vlo) : "r"(v), "r"(1u << (8 * k)));
+                else asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(vhi) : "r"(v), "r"(1u << (8 * (k - 4))));
             }
+            const uint64_t out = (uint64_t)vhi << 32 | vlo;
             __stcs(reinterpret_cast<unsigned long long *>(verdict + g * 8), (unsigned long long)out);
             if (out) {                                  // count the group's denials
                 uint64_t m = out | (out >> 4);
                 m |= m >> 2;
                 m |= m >> 1;
                 m &= 0x0101010101010101ull;             // bit 8k set iff verdict k is a denial
-                const int k = __ffsll((long long)m) - 1;
-                const uint32_t v = (uint32_t)(out >> k) & 0xFFu, w = (uint32_t)(wv >> k) & 0xFFu;
-                if (ll.cnt == 0) {
-                    ll.key = g * 8 + k / 8;
-                    ll.info = agile::pack_info(0, v, w, rid0);
-                    ll.addr = addr[g * 8 + k / 8];
-                }
+                // a lane's first denial is its smallest key; its record comes at the end
+                if (ll.cnt == 0) ll.key = g * 8 + (__ffsll((long long)m) - 1) / 8;
                 ll.cnt += __popcll(m);
             }
         } else {
@@ -121,7 +140,17 @@ k_aperture_batch(const Apertures A, const uint64_t *__restrict__ addr,
             verdict[i] = (uint8_t)v;
         }
     }
-    agile::block_log_flush(log, ll);
+    // Keys are access indices, one per access. The vector path keeps only each lane's
+    // smallest key: the block's smallest violation gets its record (verdict, width,
+    // address, aperture id) here, only once the log shows it lower.
+    agile::block_log_flush(log, ll, [&](unsigned long long k, unsigned long long &info,
+                                        unsigned long long &a) {
+        a = addr[k];
+        const uint32_t w = width[k];
+        uint32_t rid;
+        const uint32_t v = decide<N>(A, a, w, &rid);
+        info = agile::pack_info(0, v, w, rid);
+    });
 }
 
 template <int N, int VEC>
