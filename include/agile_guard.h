@@ -224,6 +224,13 @@ AGILE_API int agile_guard_table_geometry(const agile_guard_table_t *t, uint32_t 
 AGILE_API int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, void *stream,
                              agile_dev_table_t *out);
 
+/* The same image as agile_guard_table_upload, written synchronously into a caller-owned
+ * host buffer of at least device_bytes bytes, 256-byte aligned (ALIGN otherwise), with
+ * *out's pointers into that buffer: for inspecting or storing a table on the host. No
+ * GPU is used. */
+AGILE_API int agile_guard_table_image(const agile_guard_table_t *t, void *h_buf, size_t bytes,
+                                      agile_dev_table_t *out);
+
 AGILE_API void agile_guard_table_destroy(agile_guard_table_t *t);
 
 /* ---------------------------------------------------------------- host checks */

@@ -125,6 +125,7 @@ _SIG = {
     "agile_guard_table_set_remap": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "agile_guard_table_geometry": (ctypes.c_int, [_P, _P, _P]),
     "agile_guard_table_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "agile_guard_table_image": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "agile_guard_table_destroy": (None, [_P]),
     "agile_validate_args": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P]),
     "agile_validate_dma": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P]),
@@ -302,6 +303,19 @@ class Table:
         _check(lib().agile_guard_table_upload(self._h, _dptr(buf), nbytes, _stream(stream),
                                               ctypes.byref(v)), "agile_guard_table_upload")
         return DevTable(v, buf)
+
+    def image(self):
+        """agile_guard_table_image into a fresh 256-byte aligned host buffer: returns the
+        view (pointers into the buffer), the buffer's address and the image as a uint8
+        numpy array (which keeps the buffer alive)."""
+        nbytes = self.device_bytes()
+        raw = np.zeros(nbytes + 256, dtype=np.uint8)
+        off = (-raw.ctypes.data) % 256
+        img = raw[off:off + nbytes]
+        v = _DevTable()
+        _check(lib().agile_guard_table_image(self._h, ctypes.c_void_p(img.ctypes.data), nbytes,
+                                             ctypes.byref(v)), "agile_guard_table_image")
+        return v, img.ctypes.data, img
 
 
 def _range_array(base, size, kind, ident):

@@ -375,46 +375,69 @@ int agile_guard_table_geometry(const agile_guard_table_t *t, uint32_t *log2_page
     return AGILE_OK;
 }
 
+namespace {
+
+// The view of a table image whose buffer starts at `d` (device or host address).
+agile_dev_table_t view_at(const agile_guard_table &t, unsigned char *d) {
+    agile_dev_table_t h;
+    std::memset(&h, 0, sizeof h);
+    h.lo = t.lo;
+    h.npages = t.npages;
+    h.log2_page = t.log2_page;
+    h.n = t.n;
+    h.page = (const uint32_t *)(d + kTablePageOff);
+    h.base = (const uint64_t *)(d + t.off_base);
+    h.end = (const uint64_t *)(d + t.off_end);
+    h.kind = (const uint32_t *)(d + t.off_kind);
+    h.id = (const uint32_t *)(d + t.off_id);
+    h.zero_page = d + kTableZeroOff;
+    h.sink_page = d + kTableSinkOff;
+    h.bytes = t.total;
+    h.search_steps = t.search_steps;
+    h.remap_or = t.remap_or;
+    if (t.compact) h.crange = (const uint32_t *)(d + t.off_crange);
+    h.ubits = (const uint32_t *)(d + t.off_ubits);
+    h.ubits_log2 = t.ubits_log2;
+    h.ubits_n = t.ubits_n;
+    h.cmap = (const uint32_t *)(d + t.off_cmap);
+    h.cmap_log2 = t.cmap_log2;
+    h.cmap_n = t.cmap_n;
+    if (t.compact) {
+        h.cdesc = (const uint32_t *)(d + t.off_cdesc);
+        h.cdesc_log2 = t.cdesc_log2;
+        h.cdesc_k1 = t.cdesc_k1;
+        h.cdesc_k2 = t.cdesc_k2;
+    }
+    static_assert(sizeof(agile_dev_table_t) <= kTableHeaderBytes, "header fits");
+    return h;
+}
+
+}  // namespace
+
 int agile_guard_table_upload(agile_guard_table_t *t, void *d_buf, size_t bytes, void *stream,
                              agile_dev_table_t *out) {
     if (t == nullptr || d_buf == nullptr || out == nullptr) return AGILE_ERR_INVALID_ARG;
     if (bytes < t->total) return AGILE_ERR_TOO_LARGE;
     if (((uintptr_t)d_buf & 255) != 0) return AGILE_ERR_ALIGN;
-    unsigned char *d = (unsigned char *)d_buf;
-    agile_dev_table_t h;
-    std::memset(&h, 0, sizeof h);
-    h.lo = t->lo;
-    h.npages = t->npages;
-    h.log2_page = t->log2_page;
-    h.n = t->n;
-    h.page = (const uint32_t *)(d + kTablePageOff);
-    h.base = (const uint64_t *)(d + t->off_base);
-    h.end = (const uint64_t *)(d + t->off_end);
-    h.kind = (const uint32_t *)(d + t->off_kind);
-    h.id = (const uint32_t *)(d + t->off_id);
-    h.zero_page = d + kTableZeroOff;
-    h.sink_page = d + kTableSinkOff;
-    h.bytes = t->total;
-    h.search_steps = t->search_steps;
-    h.remap_or = t->remap_or;
-    if (t->compact) h.crange = (const uint32_t *)(d + t->off_crange);
-    h.ubits = (const uint32_t *)(d + t->off_ubits);
-    h.ubits_log2 = t->ubits_log2;
-    h.ubits_n = t->ubits_n;
-    h.cmap = (const uint32_t *)(d + t->off_cmap);
-    h.cmap_log2 = t->cmap_log2;
-    h.cmap_n = t->cmap_n;
-    if (t->compact) {
-        h.cdesc = (const uint32_t *)(d + t->off_cdesc);
-        h.cdesc_log2 = t->cdesc_log2;
-        h.cdesc_k1 = t->cdesc_k1;
-        h.cdesc_k2 = t->cdesc_k2;
-    }
-    static_assert(sizeof(agile_dev_table_t) <= kTableHeaderBytes, "header fits");
+    const agile_dev_table_t h = view_at(*t, (unsigned char *)d_buf);
     std::memcpy(t->staging.data(), &h, sizeof h);
     std::memset(t->staging.data() + kTableZeroOff, 0, 128);
     AGILE_CUDA_TRY(cudaMemcpyAsync(d_buf, t->staging.data(), t->total, cudaMemcpyHostToDevice,
                                    (cudaStream_t)stream));
+    *out = h;
+    return AGILE_OK;
+}
+
+int agile_guard_table_image(const agile_guard_table_t *t, void *h_buf, size_t bytes,
+                            agile_dev_table_t *out) {
+    if (t == nullptr || h_buf == nullptr || out == nullptr) return AGILE_ERR_INVALID_ARG;
+    if (bytes < t->total) return AGILE_ERR_TOO_LARGE;
+    if (((uintptr_t)h_buf & 255) != 0) return AGILE_ERR_ALIGN;
+    unsigned char *d = (unsigned char *)h_buf;
+    const agile_dev_table_t h = view_at(*t, d);
+    std::memcpy(d, t->staging.data(), t->total);
+    std::memcpy(d, &h, sizeof h);
+    std::memset(d + kTableZeroOff, 0, 128);
     *out = h;
     return AGILE_OK;
 }
