@@ -9,10 +9,12 @@ The descriptor form runs for batches that give every lane of a full grid (one 10
 block per SM) four groups of 8 accesses or more, so these batches are that large."""
 import numpy as np
 import pytest
+import torch
 
 import agile_synth as syn
 import oracle
-from gpu_util import assert_log_equal, device_table
+import paper_2606_06697_b300 as ag
+from gpu_util import DEV, assert_log_equal, device_table, new_log, to_dev
 from test_gpu_batch import run_batch
 from test_gpu_table import block_classes
 
@@ -23,7 +25,6 @@ EMPTY = 0xFFFFFFFF
 
 def desc_batch():
     """Accesses in the smallest batch that takes the descriptor form, plus a ragged 3."""
-    import torch
     return 4 * 8 * 1024 * torch.cuda.get_device_properties(0).multi_processor_count + 3
 
 
@@ -200,3 +201,31 @@ def test_batch_parity_all_open():
     assert (v == ov).all(), np.flatnonzero(v != ov)[:10]
     assert (ov == 2).mean() > 0.7                        # MMIO
     assert_log_equal(rec, olog, client=9)
+
+
+@pytest.mark.parametrize("size", ["1M", "descriptor form"])
+def test_log_accumulates_over_launches(size):
+    """Two checks into one log, in either order: the count is the sum, and the first record
+    is the one with the smaller key, whichever launch found it (the log merge lowers the
+    key word first and lets only the lowering blocks write the record)."""
+    t = syn.batch_table()
+    addr, width, label = syn.batch_accesses(t, 1 << 20)
+    m = (1 << 20) if size == "1M" else desc_batch()
+    reps = -(-m // len(addr))
+    y_a, y_w = (np.tile(x, reps)[:m] for x in (addr, width))
+    ok = int(np.flatnonzero(label == 0)[0])
+    x_a, x_w = y_a.copy(), y_w.copy()
+    x_a[:5000], x_w[:5000] = addr[ok], width[ok]       # X's first violation comes later
+    _, ox = oracle.check_batch(t, x_a, x_w, method="sorted")[::2]
+    _, oy = oracle.check_batch(t, y_a, y_w, method="sorted")[::2]
+    assert oy.key < ox.key
+    _, dev = device_table(t, 21)
+    d_v = torch.empty(m, dtype=torch.uint8, device=DEV)
+    for order in ((x_a, x_w), (y_a, y_w)), ((y_a, y_w), (x_a, x_w)):
+        log = new_log(client=2)
+        for a, w in order:
+            ag.agile_guard_check_batch(dev, to_dev(a.view(np.int64)), to_dev(w), m, d_v, log)
+        rc, rec = ag.agile_violation_log_read(log)
+        assert rec.count == ox.count + oy.count
+        assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
+            (oy.key, oy.addr, oy.width, oy.verdict, oy.range_id)
