@@ -229,3 +229,21 @@ def test_log_accumulates_over_launches(size):
         assert rec.count == ox.count + oy.count
         assert (rec.key, rec.addr, rec.width, rec.verdict, rec.range_id) == \
             (oy.key, oy.addr, oy.width, oy.verdict, oy.range_id)
+
+
+def test_batch_parity_top_of_address_space():
+    """The descriptor form on a window that ends at 2^64: accesses over its last blocks,
+    widths legal and not, some ending past 2^64 - 1 (INVALID); the block that ends at 2^64
+    has no descriptor and its accesses reach the full rule."""
+    r = top_table()
+    m = desc_batch()
+    st = syn.Stream(91, 4)
+    a = (np.uint64(2**64 - 12288) + st.below(12288, m).astype(np.uint64)).astype(np.uint64)
+    w = st.choice(np.array([1, 2, 4, 8, 16, 0, 3, 32], np.uint8), m)
+    for lg_page in (12, 21):
+        _, dev = device_table(r, lg_page)
+        v, rc, rec = run_batch(dev, a, w, client=8)
+        ov, _, olog = oracle.check_batch(r, a, w, method="sorted")
+        assert (v == ov).all(), np.flatnonzero(v != ov)[:10]
+        assert (ov == 5).any() and (ov == 0).any() and (ov == 2).any()
+        assert_log_equal(rec, olog, client=8)
