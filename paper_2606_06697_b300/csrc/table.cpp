@@ -157,11 +157,15 @@ void hash_descs(const std::vector<Desc> &d, uint32_t *lg_out, uint32_t *k1_out, 
         auto h = [&](uint32_t k, uint32_t K) { return (uint32_t)(k * K) >> (32 - lg); };
         std::vector<Desc> slot(S, Desc{0xFFFFFFFFu, 0});
         size_t placed = 0;
+        // at most 64 moves per slot in all: a table with far more open blocks than slots
+        // fills them and stops, instead of failing every remaining insertion at length
+        uint64_t moves = 64ull * S;
         for (const Desc &x : d) {
+            if (moves == 0 || placed == S) break;
             Desc cur = x;
             uint32_t pos = h(cur.block, k1);
             bool ok = false;
-            for (int kick = 0; kick < 64; ++kick) {
+            for (int kick = 0; kick < 64 && moves > 0; ++kick, --moves) {
                 if (slot[pos].block == 0xFFFFFFFFu) { slot[pos] = cur; ok = true; break; }
                 std::swap(cur, slot[pos]);
                 const uint32_t a1 = h(cur.block, k1);
