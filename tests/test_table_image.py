@@ -87,3 +87,22 @@ def test_image_arguments():
                                        t.device_bytes(), ctypes.byref(v)) == -12
     assert lib.agile_guard_table_image(None, p, t.device_bytes(), ctypes.byref(v)) == -1
     assert lib.agile_guard_table_image(t.handle, p, t.device_bytes(), ctypes.byref(v)) == 0
+
+
+def test_image_descriptors_all_open_window():
+    """A 1 GiB MMIO range with allocations after it: every block of the MMIO range is open
+    and describable, far more than the 4096 slots. The build stays quick, fills the slots
+    and stores only correct descriptors."""
+    import time
+    base = 0x7D0000000000
+    r = syn._ranges([base, base + (1 << 30), base + (1 << 30) + 8192], [1 << 30, 4096, 100000],
+                    [syn.KIND_MMIO, syn.KIND_USER, syn.KIND_PROTECTED], [1, 2, 3])
+    t0 = time.perf_counter()
+    t, v, addr, img = image(r, 21)
+    assert time.perf_counter() - t0 < 10.0
+    want = expected_descs(r, v.lo, v.cmap_log2, v.cmap_n)
+    assert len(want) > 4 * 4096 and v.cdesc_log2 == 12
+    slots = section(img, addr, v.cdesc, 8 << v.cdesc_log2).view(np.uint32).reshape(-1, 2)
+    held = [(k, p) for k, p in slots.tolist() if k != EMPTY]
+    assert len(held) > 3 * 4096 // 4
+    assert all(want[k] == p for k, p in held)
